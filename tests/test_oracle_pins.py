@@ -367,3 +367,16 @@ def test_no_lookback_speed_is_lab_frame():
         cents.append(float((img.sum(axis=1) * q).sum() / img.sum()))
     speed = np.polyfit(ts, cents, 1)[0]
     assert speed == pytest.approx(beta_z * math.sin(math.radians(theta)), rel=0.01)
+
+
+@pytest.mark.parametrize("t_obs,epoch", [(-40.0, 0), (1000.0, -1)])
+def test_fast_light_clamps_to_end_epochs(t_obs, epoch):
+    """Without lookback an observer time before the first (after the last)
+    snapshot reads the first (last) one: the single-snapshot render of that
+    epoch (reading A8 of Eq. 10's fast-light limit)."""
+    grid, j, beta = _random_tiny(11, M=4)
+    v = gen.view_from_angles(grid, 47.0, 12.0, size=6, t_obs=t_obs, lookback=False)
+    single = gen.Grid(n=grid.n, origin=grid.origin, dx=grid.dx, n_epochs=1, t0=0.0, dt=1.0)
+    a = oracle.render(grid, j, beta, v)
+    b = oracle.render(single, j[epoch:][:1] if epoch >= 0 else j[-1:], beta[-1:] if epoch < 0 else beta[:1], v)
+    assert np.array_equal(a, b)
