@@ -26,8 +26,8 @@
  *      chord midpoint, with s measured from the image plane through the view
  *      centre (readings A3, A4);
  *   6. the temporal weights are the linear kernel W_{n,m} = 1 - delta_{n,m} for
- *      m in {m_bar, m_bar+1}, zero otherwise (Eqs. 6-8, Sec. 2.3); a time
- *      outside the stored epochs contributes nothing (reading A6); without
+ *      m in {m_bar, m_bar+1}, zero otherwise (Eqs. 6-8, Sec. 2.3), summed over
+ *      the stored snapshots m = 0 .. M-1 only (Eq. 9; reading A6); without
  *      lookback every cell is read at t_obs (Eq. 3, Eq. 10) with the epoch
  *      coordinate clamped to the stored range (reading A8);
  *   7. D = 1/(Gamma (1 + beta . s_hat)), Gamma = 1/sqrt(1 - beta^2) (Eq. 14),
@@ -41,7 +41,10 @@
  *       integer, so that the piecewise-linear weight is integrated exactly.
  *   A4  s is measured from the plane through the view centre, normal to s_hat.
  *   A5  orthographic projection (observer at infinity).
- *   A6  t_bar outside [t_0, t_{M-1}] contributes zero (lookback only).
+ *   A6  the sum over m in Eq. 9 runs over the stored snapshots.  A time
+ *       within one cadence before t_0 (after t_{M-1}) keeps the weight
+ *       1 - delta of the first (last) snapshot, fading linearly to zero; a time
+ *       further out contributes nothing.  The sum is continuous in t_bar.
  *   A8  fast light: every cell at t_obs, epoch coordinate clamped to [0, M-1].
  *   A11 a point exactly on a face belongs to the cell on the + side (floor).
  *   A12 pixel (p, q) centre at ((p + 1/2 - W/2) h_u, (q + 1/2 - H/2) h_v) on the
@@ -122,16 +125,16 @@ static int camera_basis(const orc_view *v, double sh[3], double eu[3], double ev
     return ORC_OK;
 }
 
-/* W_{n,m} D_{n,m}^{2-alpha} j'_{n,m}, summed over m, for one cell at epoch
- * coordinate u = (t_bar - t0)/dt (Eqs. 6-8 and 14, 19).  Returns 0 and sets
- * *inside = 0 when the time lies outside the stored epochs under lookback. */
+/* W_{n,m} D_{n,m}^{2-alpha} j'_{n,m}, summed over the stored m, for one cell
+ * at epoch coordinate u = (t_bar - t0)/dt (Eqs. 6-9 and 14, 19).  *inside is
+ * set when at least one stored snapshot has a nonzero weight. */
 static double cell_value(const orc_grid *g, const orc_fields *f, const orc_view *v,
                          const double sh[3], size_t cell, double u, int *inside)
 {
     const int M = g->n_epochs;
     const size_t ncell = (size_t)g->n[0] * g->n[1] * g->n[2];
     if (v->lookback) {
-        if (!(u >= 0.0 && u <= (double)(M - 1))) { *inside = 0; return 0.0; }
+        if (!(u > -1.0 && u < (double)M)) { *inside = 0; return 0.0; }
     } else {
         if (u < 0.0) u = 0.0;
         if (u > (double)(M - 1)) u = (double)(M - 1);
@@ -141,7 +144,7 @@ static double cell_value(const orc_grid *g, const orc_fields *f, const orc_view 
     double sum = 0.0;
     for (int k = 0; k < 2; ++k) {
         double m = mbar + k;
-        if (m > (double)(M - 1)) continue;
+        if (m < 0.0 || m > (double)(M - 1)) continue;   /* stored snapshots only */
         double w = 1.0 - fabs(u - m);          /* Eq. 7 with Eq. 6 */
         if (!(w > 0.0)) continue;
         size_t idx = (size_t)m * ncell + cell;
@@ -169,7 +172,7 @@ static double epoch_coord(const orc_grid *g, const orc_view *v, double s)
 }
 
 /* One pixel: returns the intensity and the number of positive-length cell
- * chords that lie inside the temporal window (the "cell-samples"). */
+ * chords with a nonzero temporal weight (the "cell-samples"). */
 static double render_pixel(const orc_grid *g, const orc_fields *f, const orc_view *v,
                            const double sh[3], const double eu[3], const double ev[3],
                            int p, int q, double *crossings, int64_t *count)

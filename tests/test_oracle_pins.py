@@ -184,11 +184,9 @@ def _brute_force_pixel(grid, j, beta, view, p, q, e_u, e_v, h=1e-4):
     M = grid.n_epochs
     tbar = view.t_obs - s / view.c if view.lookback else np.full_like(s, view.t_obs)
     u = (tbar - grid.t0) / grid.dt
-    if view.lookback:
-        keep = (u >= 0) & (u <= M - 1)
-        s, idx, u = s[keep], idx[keep], u[keep]
-    else:
+    if not view.lookback:
         u = np.clip(u, 0, M - 1)
+    # Eq. 9: the hat weights of Eq. 7 summed over the stored snapshots only
     total = 0.0
     n_hat = -s_hat
     for m in range(M):
@@ -302,7 +300,8 @@ def test_frequency_scaling():
 
 
 def test_outside_window_is_dark():
-    """Lookback: a time outside the stored epochs contributes nothing."""
+    """Lookback: a time more than one cadence outside the stored epochs
+    contributes nothing."""
     grid, j, beta = _random_tiny(10)
     v = gen.view_from_angles(grid, 40.0, 10.0, size=6, t_obs=500.0, c=1.0)
     assert np.all(oracle.render(grid, j, beta, v) == 0.0)
@@ -380,3 +379,16 @@ def test_fast_light_clamps_to_end_epochs(t_obs, epoch):
     a = oracle.render(grid, j, beta, v)
     b = oracle.render(single, j[epoch:][:1] if epoch >= 0 else j[-1:], beta[-1:] if epoch < 0 else beta[:1], v)
     assert np.array_equal(a, b)
+
+
+def test_window_edge_fades_linearly():
+    """Eq. 9 sums Eq. 7's weights over the stored snapshots, so a time just
+    past the last snapshot keeps weight 1 - delta on it (continuity in t_bar)."""
+    M, dt = 4, 2.0
+    grid = gen.Grid(n=(1, 1, 1), n_epochs=M, t0=0.0, dt=dt)
+    j = np.zeros((M, 1, 1, 1))
+    j[M - 1] = 1.0
+    j[0] = 10.0
+    v = _view(grid, (0, 0, -1), (0, 1, 0), c=1.0, lookback=True)
+    for t_obs, expect in ((6.0, 1.0), (6.5, 0.75), (7.9, 0.05), (8.0, 0.0), (-0.5, 7.5), (-2.0, 0.0)):
+        assert oracle.render(grid, j, None, v.with_(t_obs=t_obs))[0, 0] == pytest.approx(expect, abs=1e-12)
