@@ -197,7 +197,7 @@ def config_tiny(seed: int = 1):
 
 
 def config_time_delay(seed: int = 2, n: int = 256, n_epochs: int = 16, size: int = 512,
-                      thetas=(10.0, 45.0), n_tobs: int = 9):
+                      thetas=(10.0, 45.0), n_tobs: int = 9, dtype=np.float64):
     """Moving Gaussian blob (sigma = n/32) over a steady conical jet, both at
     beta = 0.95 z; c dt = 4 cells so the blob moves 3.8 cells per epoch.
     Views: every theta x ``n_tobs`` observer times whose blob-centre retarded
@@ -208,11 +208,12 @@ def config_time_delay(seed: int = 2, n: int = 256, n_epochs: int = 16, size: int
     sigma = 8.0 * s
     start = np.array([grid.center[0], grid.center[1], 64.0 * s])
     jet = 0.1 * conical_jet(grid, seed)
-    j = np.empty((n_epochs, n, n, n), dtype=np.float64)
+    j = np.empty((n_epochs, n, n, n), dtype=dtype)
     for m in range(n_epochs):
         pos = start + np.array([0.0, 0.0, beta_z * c * dt * m])
         j[m] = jet + gaussian_blob(grid, pos, sigma, 1.0)
-    _, beta = uniform_fields(grid, 0.0, (0.0, 0.0, beta_z))
+    beta = np.zeros((n_epochs, n, n, n, 3), dtype=dtype)
+    beta[..., 2] = beta_z
     views = []
     lo, hi = 3.0 * (n_epochs - 1) / 15.0, 12.0 * (n_epochs - 1) / 15.0
     for th in thetas:

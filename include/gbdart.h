@@ -1,0 +1,257 @@
+/*
+ * gbdart.h -- C ABI of the GB300 relativistic ray-marching library.
+ *
+ * The library renders synthetic observations of optically thin emission from
+ * meshed simulation snapshots: for every pixel of an orthographic camera it
+ * sums, along the pixel's line of sight, the rest-frame emissivity boosted by
+ * the Doppler factor and read at the retarded time of each cell,
+ *
+ *   I_nu = (nu/nu'_0)^alpha sum_m sum_n W_{n,m} D_{n,m}^{2-alpha} j'_{n,m} ds_n
+ *
+ * (Whitehead, Elley & Everett, "cuDART", Eq. 19 of Sec. 2.5; the cell chords
+ * ds_n of Sec. 2.4; the temporal weights W of Eqs. 6-7, Sec. 2.3; the Doppler
+ * factor D of Eq. 14; the retarded time t_bar = t_obs - s/c of Eq. 2).
+ *
+ * Conventions shared by every entry point
+ * ----------------------------------------
+ *  - Every call returns an int status (GBD_OK = 0 or a GBD_ERR_* code) and never
+ *    throws, aborts or exits.  gbd_last_error() gives a message for the last
+ *    failing call on the calling thread.
+ *  - A context is bound to one CUDA device.  It is internally locked: calls from
+ *    several host threads are serialised on the host, while the GPU work they
+ *    enqueue may overlap when issued on different streams.
+ *  - Streams are passed as `void *` holding a cudaStream_t (NULL = the legacy
+ *    default stream).  Rendering calls are asynchronous on that stream; the
+ *    caller synchronises before reading the image.
+ *  - Lengths are in grid units (cells of size dx along each axis), times in the
+ *    same unit system; c is the signal speed in those units (cells per unit
+ *    time when dx = 1).
+ *  - The sign convention for alpha is the paper's: rest-frame emissivity
+ *    j' ~ nu'^alpha, so the default synchrotron slope is alpha = -0.6 and the
+ *    per-cell boost is D^(2 - alpha) = D^2.6.
+ *
+ * Geometry of a view (readings of the paper, which does not fix the camera):
+ *  - dir is the unit viewing direction s_hat, pointing from the observer into
+ *    the scene; the direction to the observer is n_hat = -s_hat, so
+ *    D = 1 / (Gamma (1 + beta . s_hat)) = 1 / (Gamma (1 - beta . n_hat)).
+ *  - The camera is orthographic.  The image plane passes through `center` and is
+ *    normal to s_hat; s is measured from that plane, so t_bar = t_obs - s/c.
+ *  - e_v is `up` projected onto the image plane and normalised, e_u = s_hat x e_v.
+ *    Pixel (p, q) has its centre at center + (p + 1/2 - W/2) h_u e_u +
+ *    (q + 1/2 - H/2) h_v e_v with h_u = fov_u / W, h_v = fov_v / H, and is stored
+ *    at out[q * W + p] (row q = 0 is the bottom row).
+ *  - The temporal weight of a cell uses t_bar at the midpoint of its chord.
+ *    The weights W_{n,m} = 1 - |t_bar - t_m| / dt (for the two snapshots that
+ *    bracket t_bar) are summed over the stored snapshots only, so a t_bar
+ *    within one cadence outside [t_0, t_{M-1}] keeps a linearly fading weight
+ *    on the end snapshot and anything further out contributes nothing.
+ *    Without GBD_LOOKBACK every cell is read at t_obs, clamped to
+ *    [t_0, t_{M-1}].
+ */
+#ifndef GBDART_H
+#define GBDART_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------------ status */
+enum {
+    GBD_OK = 0,
+    GBD_ERR_INVALID = 1,   /* bad argument or bad field value                 */
+    GBD_ERR_NOMEM = 2,     /* a device or pinned host allocation failed        */
+    GBD_ERR_BUDGET = 3,    /* the request can never fit the context's HBM budget */
+    GBD_ERR_NOTFOUND = 4,  /* unknown volume handle or ticket                  */
+    GBD_ERR_TIMEOUT = 5,   /* a bounded wait ran out                           */
+    GBD_ERR_CUDA = 6,      /* a CUDA runtime call failed (message has details) */
+    GBD_ERR_CANCELLED = 7, /* the request was cancelled                        */
+    GBD_ERR_BUSY = 8       /* the resource is in use (e.g. unload while queued)*/
+};
+
+/* Input precision of the snapshot arrays handed to gbd_load_snapshots. */
+enum { GBD_IN_F64 = 0, GBD_IN_F32 = 1 };
+
+/* Storage format of the packed volume on the device.
+ *  GBD_STORE_F32:      16-byte record {j', beta_x, beta_y, beta_z} in float32.
+ *  GBD_STORE_BF16_F16U: 8-byte record {bfloat16 j', float16 u_x, u_y, u_z} with
+ *                      u = Gamma beta, the spatial four-velocity.  j' is rounded
+ *                      to float32 then to bfloat16 (nearest even); u is computed
+ *                      in float64 from the input and rounded once to float16.  The
+ *                      four-velocity keeps the Doppler factor well conditioned
+ *                      as |beta| -> 1; the arithmetic still accumulates in
+ *                      float32. */
+enum { GBD_STORE_F32 = 0, GBD_STORE_BF16_F16U = 1 };
+
+/* View flags: routine A of the paper is 0, routine B is GBD_BEAMING, routine C
+ * (the default of the paper) is GBD_BEAMING | GBD_LOOKBACK (Sec. 3, Table 1). */
+enum { GBD_BEAMING = 1u, GBD_LOOKBACK = 2u };
+
+typedef struct gbd_ctx gbd_ctx;
+typedef uint64_t gbd_volume;
+
+/* Uniform Cartesian mesh in the lab frame and its snapshot cadence
+ * (Sec. 2.3: t_m = t_0 + m dt; Sec. 2.4: cells need not be cubic). */
+typedef struct {
+    int32_t n[3];        /* cells along x, y, z (each >= 1, <= 4096)        */
+    double origin[3];    /* lower corner of cell (0, 0, 0)                  */
+    double dx[3];        /* cell edge along x, y, z (> 0)                   */
+    int32_t n_epochs;    /* M >= 1 snapshots                                */
+    double t0, dt;       /* epoch m at t0 + m dt; dt > 0                    */
+} gbd_grid;
+
+/* The three inputs of the method (Sec. 2.5): rest-frame emissivity j' and
+ * velocity beta = v/c per cell and epoch; alpha is given per view.
+ *  j   : [M][n_z][n_y][n_x]     C order, x fastest
+ *  vel : [M][n_z][n_y][n_x][3]  C order, components (x, y, z)
+ * Both are read during the call only; the caller keeps ownership.  When
+ * on_device is nonzero both are device pointers on the context's device,
+ * otherwise host pointers.  j' < 0, non-finite values or |beta| >= 1 reject
+ * the whole load with GBD_ERR_INVALID. */
+typedef struct {
+    const void *j;
+    const void *vel;
+    int32_t dtype_in;    /* GBD_IN_F64 or GBD_IN_F32                        */
+    int32_t store;       /* GBD_STORE_F32 or GBD_STORE_BF16_F16U            */
+    int32_t on_device;
+    int32_t brick;       /* layout: brick edge 4 or 8; 0 = library default  */
+    int32_t super_brick; /* bricks per super-brick edge 1, 2 or 4; 0 = default */
+} gbd_fields;
+
+/* One observation (Secs. 2.1-2.2, 2.5). */
+typedef struct {
+    double dir[3];       /* viewing direction s_hat into the scene (any length > 0) */
+    double up[3];        /* image up before projection; not parallel to dir  */
+    double center[3];    /* image-plane centre; s = 0 there                  */
+    double t_obs;        /* observer time                                    */
+    double c;            /* signal speed; may be +infinity (fast-light limit) */
+    double alpha;        /* rest-frame spectral slope (paper sign, e.g. -0.6) */
+    double nu_ratio;     /* nu / nu'_0 > 0 (Eq. 20)                          */
+    uint32_t flags;      /* GBD_BEAMING | GBD_LOOKBACK                       */
+} gbd_view;
+
+/* Image geometry and destination.  out holds width*height floats (per view
+ * for batch calls, views stored one after another).  out is a device pointer
+ * unless out_on_host is nonzero, in which case the library renders into its
+ * own device buffer and copies the image to the host pointer on the stream
+ * (pinned host memory makes that copy asynchronous).  samples, if not NULL,
+ * is a device array receiving per pixel the number of cell-samples (cells
+ * with a positive chord and a nonzero temporal weight); it is ignored when
+ * out_on_host is set. */
+typedef struct {
+    int32_t width, height;   /* pixels, each in [1, 16384]                  */
+    double fov_u, fov_v;     /* image extent along e_u and e_v (> 0)        */
+    float *out;
+    uint32_t *samples;
+    int32_t out_on_host;
+} gbd_image_spec;
+
+/* Launch configuration of the march kernels (chosen by gbd_tune or given). */
+typedef struct {
+    int32_t packet_w, packet_h;  /* pixels of one warp packet: 8x4, 4x8, 16x2, 32x1 */
+    int32_t cta_warps;           /* warps per CTA: 1, 2, 4 or 8                     */
+    int32_t depth;               /* cells gathered ahead per lane: 1, 2 or 4       */
+    int32_t persistent;          /* 1 = persistent grid over a tile queue           */
+} gbd_launch;
+
+/* Description of a resident volume. */
+typedef struct {
+    gbd_grid grid;
+    int32_t store;
+    int32_t brick, super_brick;
+    uint64_t bytes;          /* device bytes held by the packed volume       */
+    uint64_t record_bytes;   /* 16 (F32) or 8 (BF16_F16U)                    */
+} gbd_volume_desc;
+
+/* ------------------------------------------------------------ errors */
+/* Static text for a status code. */
+const char *gbd_error_string(int status);
+/* Message of the last failing call made on this thread ("" if none).  The
+ * pointer stays valid until the next call on the same thread. */
+const char *gbd_last_error(void);
+
+/* ------------------------------------------------------------ context */
+/* Creates a context on CUDA device `device`.  hbm_budget_bytes caps the device
+ * memory the context may hold for packed volumes, render buffers and queued
+ * requests (0 = 90% of the device's free memory at creation).  *out receives
+ * the context, or NULL on failure. */
+int gbd_create(gbd_ctx **out, int32_t device, uint64_t hbm_budget_bytes);
+/* Waits for the context's outstanding work, frees everything it holds and the
+ * context itself.  NULL is accepted. */
+int gbd_destroy(gbd_ctx *ctx);
+
+/* ------------------------------------------------------------ volumes */
+/* Validates the fields, copies them to the device if needed and packs them
+ * into the bricked record layout (device work on an internal stream, finished
+ * before the call returns).  *out receives a handle owned by the context until
+ * gbd_unload.  GBD_ERR_BUDGET if the packed volume does not fit the budget. */
+int gbd_load_snapshots(gbd_ctx *ctx, const gbd_grid *grid, const gbd_fields *fields, gbd_volume *out);
+/* Frees a volume.  GBD_ERR_BUSY if queued serving requests still use it. */
+int gbd_unload(gbd_ctx *ctx, gbd_volume vol);
+int gbd_volume_info(gbd_ctx *ctx, gbd_volume vol, gbd_volume_desc *out);
+
+/* ------------------------------------------------------------ rendering */
+/* Renders one view into spec->out (Eq. 19 for every pixel), asynchronously on
+ * `stream`.  launch may be NULL (tuned or default configuration). */
+int gbd_render(gbd_ctx *ctx, gbd_volume vol, const gbd_view *view, const gbd_image_spec *spec,
+               const gbd_launch *launch, void *stream);
+
+/* Renders n views of the same image geometry in one persistent launch over a
+ * shared tile queue; view k goes to spec->out + k * width * height (and the
+ * sample counts likewise).  The view table and the queue counter live in a
+ * context-owned device buffer; the launch is captured once into a CUDA graph
+ * per (volume, n, geometry, destination, launch) and replayed afterwards.
+ * Concurrent batch calls on one context are serialised on the context's lock,
+ * and the GPU work of consecutive calls is ordered on their streams. */
+int gbd_render_batch(gbd_ctx *ctx, gbd_volume vol, const gbd_view *views, int32_t n,
+                     const gbd_image_spec *spec, const gbd_launch *launch, void *stream);
+
+/* Number of kernels the last successful render call of this thread
+ * launched (graph replays count their kernels). */
+int32_t gbd_last_launch_count(void);
+
+/* ------------------------------------------------------------ autotuning
+ * The paper runs one kernel shape; the launch configuration (warp packet
+ * shape, warps per CTA, cells gathered ahead per lane) and the volume layout
+ * (brick and super-brick edge) are tuned here per class of render: grid
+ * dimensions, storage, snapshot count, image size, batch size and lookback.
+ */
+enum { GBD_TUNE_LAUNCH = 1u, GBD_TUNE_LAYOUT = 2u };
+
+typedef struct {
+    gbd_launch launch;       /* best launch configuration found            */
+    int32_t brick;           /* layout of the volume after tuning          */
+    int32_t super_brick;
+    float ms;                /* median time of the best candidate          */
+    int32_t candidates;      /* configurations timed                       */
+} gbd_tune_result;
+
+/* Times candidate configurations for rendering `views` (as gbd_render_batch
+ * would, writing into spec->out, which must be device memory) on `stream`
+ * and synchronises it.  With GBD_TUNE_LAYOUT the volume is re-packed on the
+ * device into each candidate layout and left in the fastest one (the handle
+ * stays valid; the re-pack needs room for a second copy within the budget).
+ * The best launch configuration is remembered by the context and used by
+ * gbd_render and gbd_render_batch calls of the same class that pass
+ * launch = NULL.  With the environment variable GBD_TUNE_CACHE naming a file,
+ * results are appended to it and read back by later contexts. */
+int gbd_tune(gbd_ctx *ctx, gbd_volume vol, const gbd_view *views, int32_t n, const gbd_image_spec *spec,
+             uint32_t what, void *stream, gbd_tune_result *out);
+
+/* Re-packs a volume into another layout on the device (brick 1, 2, 4 or 8;
+ * super_brick 1, 2 or 4), keeping its handle.  Waits for the device. */
+int gbd_relayout(gbd_ctx *ctx, gbd_volume vol, int32_t brick, int32_t super_brick);
+
+/* Bounds checking.  In the library built with GBD_CHECKED every gather tests
+ * its cell and epoch index against the volume; a violation skips the load and
+ * sets a device word instead of faulting.  This call waits for the device,
+ * stores that word in *out (0 = no violation; always 0 in the production
+ * build) and clears it. */
+int gbd_bounds_violations(gbd_ctx *ctx, int32_t *out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GBDART_H */

@@ -1,0 +1,719 @@
+// api.cpp -- host runtime behind the C ABI of include/gbdart.h.
+//
+// Owns contexts, the registry of packed volumes, the per-view set-up done in
+// float64 on the host (camera basis, pixel pitch, lookback window, power-law
+// prefactor), HBM budget accounting, the cached CUDA graphs of batch renders,
+// and error reporting.  All device work is issued through the kernels of
+// march.cu and pack.cu.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "gbd_internal.h"
+#include "runtime.h"
+
+namespace gbd {
+
+// ------------------------------------------------------------------ errors
+namespace {
+thread_local std::string t_last_error;
+thread_local int32_t t_last_launches = 0;
+}  // namespace
+
+int fail(int code, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    std::vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    t_last_error = buf;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char *what)
+{
+    cudaGetLastError();  // clear a sticky-free error so later calls can proceed
+    if (e == cudaErrorMemoryAllocation) return fail(GBD_ERR_NOMEM, "%s: %s", what, cudaGetErrorString(e));
+    return fail(GBD_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+void set_launch_count(int32_t n) { t_last_launches = n; }
+
+DeviceGuard::DeviceGuard(int dev)
+{
+    cudaGetDevice(&prev_);
+    if (prev_ != dev) cudaSetDevice(dev);
+}
+DeviceGuard::~DeviceGuard()
+{
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (cur != prev_) cudaSetDevice(prev_);
+}
+
+// ------------------------------------------------------------------ layout
+// Per-axis offset tables of the bricked layout.  With brick edge B and
+// super-brick edge S (in bricks), the grid is padded to multiples of B*S; the
+// super-bricks are stored in x-fastest order, the S^3 bricks inside a
+// super-brick in Morton order, and the B^3 cells inside a brick x-fastest.
+// Each of the three contributions is a function of one axis only, so the
+// record offset is tab_x[ix] + tab_y[iy] + tab_z[iz].  B = S = 1 gives the
+// plain C-ordered layout.
+static uint32_t spread3(uint32_t v)
+{
+    uint32_t r = 0;
+    for (int b = 0; b < 10; ++b) r |= ((v >> b) & 1u) << (3 * b);
+    return r;
+}
+
+bool build_layout(const int n[3], int B, int S, std::vector<int32_t> &tab, long long &epoch_stride)
+{
+    const long long E = static_cast<long long>(B) * S;
+    long long P[3], NS[3];
+    for (int a = 0; a < 3; ++a) {
+        P[a] = (n[a] + E - 1) / E * E;
+        NS[a] = P[a] / E;
+    }
+    const long long super_vol = E * E * E;
+    epoch_stride = NS[0] * NS[1] * NS[2] * super_vol;
+    if (epoch_stride >= (1LL << 31)) return false;
+    const long long B3 = static_cast<long long>(B) * B * B;
+    const long long super_stride[3] = {super_vol, NS[0] * super_vol, NS[0] * NS[1] * super_vol};
+    const long long cell_stride[3] = {1, B, static_cast<long long>(B) * B};
+    tab.resize(static_cast<size_t>(n[0] + n[1] + n[2]));
+    size_t w = 0;
+    for (int a = 0; a < 3; ++a) {
+        for (int i = 0; i < n[a]; ++i) {
+            const long long sup = i / E;
+            const uint32_t bin = static_cast<uint32_t>((i / B) % S);
+            const long long morton = static_cast<long long>(spread3(bin)) << a;
+            tab[w++] = static_cast<int32_t>(sup * super_stride[a] + morton * B3 + (i % B) * cell_stride[a]);
+        }
+    }
+    return true;
+}
+
+// ------------------------------------------------------------------ views
+static bool finite3(const double v[3]) { return std::isfinite(v[0]) && std::isfinite(v[1]) && std::isfinite(v[2]); }
+
+int make_view(const Volume &vol, const gbd_view &v, int width, int height, double fov_u, double fov_v, ViewDev &out)
+{
+    if (!finite3(v.dir) || !finite3(v.up) || !finite3(v.center) || !std::isfinite(v.t_obs) ||
+        !std::isfinite(v.alpha) || !(v.nu_ratio > 0.0) || !std::isfinite(v.nu_ratio) || std::isnan(v.c) ||
+        !(v.c > 0.0))
+        return fail(GBD_ERR_INVALID, "view: non-finite or out-of-range parameter");
+    if ((v.flags & ~(GBD_BEAMING | GBD_LOOKBACK)) != 0u) return fail(GBD_ERR_INVALID, "view: unknown flag bits");
+    if (width < 1 || height < 1 || width > 16384 || height > 16384)
+        return fail(GBD_ERR_INVALID, "image: width/height must be in [1, 16384]");
+    if (!(fov_u > 0.0) || !(fov_v > 0.0) || !std::isfinite(fov_u) || !std::isfinite(fov_v))
+        return fail(GBD_ERR_INVALID, "image: fov must be positive and finite");
+    double sh[3], ev[3], eu[3];
+    const double nd = std::sqrt(v.dir[0] * v.dir[0] + v.dir[1] * v.dir[1] + v.dir[2] * v.dir[2]);
+    if (!(nd > 0.0)) return fail(GBD_ERR_INVALID, "view: zero direction");
+    for (int i = 0; i < 3; ++i) sh[i] = v.dir[i] / nd;
+    // Components below 1e-20 are treated as exactly zero (the ray never
+    // crosses a face of that axis within any representable grid).
+    for (int i = 0; i < 3; ++i)
+        if (std::fabs(sh[i]) < 1e-20) sh[i] = 0.0;
+    const double us = v.up[0] * sh[0] + v.up[1] * sh[1] + v.up[2] * sh[2];
+    for (int i = 0; i < 3; ++i) ev[i] = v.up[i] - us * sh[i];
+    const double nv = std::sqrt(ev[0] * ev[0] + ev[1] * ev[1] + ev[2] * ev[2]);
+    if (!(nv > 1e-12)) return fail(GBD_ERR_INVALID, "view: up is parallel to dir");
+    for (int i = 0; i < 3; ++i) ev[i] /= nv;
+    eu[0] = sh[1] * ev[2] - sh[2] * ev[1];
+    eu[1] = sh[2] * ev[0] - sh[0] * ev[2];
+    eu[2] = sh[0] * ev[1] - sh[1] * ev[0];
+    const double hu = fov_u / width, hv = fov_v / height;
+    const double a0 = (0.5 - 0.5 * width) * hu, b0 = (0.5 - 0.5 * height) * hv;
+    std::memset(&out, 0, sizeof(out));
+    for (int i = 0; i < 3; ++i) {
+        out.r00[i] = v.center[i] + a0 * eu[i] + b0 * ev[i];
+        out.du[i] = hu * eu[i];
+        out.dv[i] = hv * ev[i];
+        out.sh[i] = sh[i];
+        out.inv_sh[i] = sh[i] != 0.0 ? 1.0 / sh[i] : 0.0;
+        out.inv_sh_f[i] = sh[i] != 0.0 ? static_cast<float>(1.0 / sh[i]) : 0.0f;
+        out.sh_hi[i] = static_cast<float>(sh[i]);
+        out.sh_lo[i] = static_cast<float>(sh[i] - static_cast<double>(out.sh_hi[i]));
+    }
+    const int M = vol.grid.n_epochs;
+    const double t0 = vol.grid.t0, dt = vol.grid.dt;
+    out.t_obs = v.t_obs;
+    out.flags = v.flags;
+    out.expo = static_cast<float>(2.0 - v.alpha);
+    out.prefactor = static_cast<float>(std::pow(v.nu_ratio, v.alpha));
+    const double inf = HUGE_VAL;
+    if (v.flags & GBD_LOOKBACK) {
+        if (std::isinf(v.c)) {
+            out.inv_c = 0.0;
+            const double u = (v.t_obs - t0) / dt;
+            const bool any = u > -1.0 && u < static_cast<double>(M);
+            out.win_lo = any ? -inf : inf;
+            out.win_hi = any ? inf : -inf;
+        } else {
+            // Retarded times inside (t0 - dt, t0 + M dt) reach a stored
+            // snapshot (Eq. 9 over stored m); s = c (t_obs - t_bar).
+            out.inv_c = 1.0 / v.c;
+            const double lo = v.c * (v.t_obs - t0 - M * dt), hi = v.c * (v.t_obs - t0 + dt);
+            const double slack = 1e-9 * (std::fabs(lo) + std::fabs(hi)) + 1e-9;
+            out.win_lo = lo - slack;
+            out.win_hi = hi + slack;
+        }
+        out.u_fast = 0.0f;
+    } else {
+        out.inv_c = 0.0;
+        out.win_lo = -inf;
+        out.win_hi = inf;
+        double u = (v.t_obs - t0) / dt;
+        u = std::min(std::max(u, 0.0), static_cast<double>(M - 1));
+        out.u_fast = static_cast<float>(u);
+        // the float rounding of u must not leave [0, M-1]
+        if (out.u_fast > static_cast<float>(M - 1)) out.u_fast = static_cast<float>(M - 1);
+    }
+    if (!(out.prefactor > 0.0f) || !std::isfinite(out.prefactor))
+        return fail(GBD_ERR_INVALID, "view: nu_ratio^alpha is not a positive float");
+    return GBD_OK;
+}
+
+VolDev vol_dev(const Volume &v)
+{
+    VolDev d;
+    std::memset(&d, 0, sizeof(d));
+    d.rec = v.rec;
+    d.axis_off = v.axis_off;
+    d.epoch_stride = v.epoch_stride;
+    for (int i = 0; i < 3; ++i) {
+        d.n[i] = v.grid.n[i];
+        d.origin[i] = v.grid.origin[i];
+        d.dx[i] = v.grid.dx[i];
+        d.inv_dx[i] = 1.0 / v.grid.dx[i];
+    }
+    d.M = v.grid.n_epochs;
+    d.t0 = v.grid.t0;
+    d.inv_dt = 1.0 / v.grid.dt;
+    d.store = v.store;
+    return d;
+}
+
+LaunchCfg resolve_launch(const gbd_launch *l)
+{
+    LaunchCfg c{8, 4, 8, 2, 1};
+    if (l) {
+        if (l->packet_w > 0) c.packet_w = l->packet_w;
+        if (l->packet_h > 0) c.packet_h = l->packet_h;
+        if (l->cta_warps > 0) c.cta_warps = l->cta_warps;
+        if (l->depth > 0) c.depth = l->depth;
+        c.persistent = l->persistent != 0;
+    }
+    return c;
+}
+
+int check_launch(const LaunchCfg &c)
+{
+    if (c.packet_w * c.packet_h != 32 || c.packet_w < 1 || c.packet_h < 1)
+        return fail(GBD_ERR_INVALID, "launch: packet_w * packet_h must be 32");
+    if (c.cta_warps != 1 && c.cta_warps != 2 && c.cta_warps != 4 && c.cta_warps != 8)
+        return fail(GBD_ERR_INVALID, "launch: cta_warps must be 1, 2, 4 or 8");
+    if (c.depth != 1 && c.depth != 2 && c.depth != 4) return fail(GBD_ERR_INVALID, "launch: depth must be 1, 2 or 4");
+    return GBD_OK;
+}
+
+int check_spec(const gbd_image_spec *s)
+{
+    if (!s) return fail(GBD_ERR_INVALID, "image spec is NULL");
+    if (s->width < 1 || s->height < 1 || s->width > 16384 || s->height > 16384)
+        return fail(GBD_ERR_INVALID, "image: width/height must be in [1, 16384]");
+    if (!s->out) return fail(GBD_ERR_INVALID, "image: out is NULL");
+    return GBD_OK;
+}
+
+void fill_args(MarchArgs &a, const Volume &vol, const ViewDev *d_views, int n, const gbd_image_spec &s,
+               float *out, uint32_t *samples, int *queue, const LaunchCfg &cfg, int *err_word)
+{
+    std::memset(&a, 0, sizeof(a));
+    a.vol = vol_dev(vol);
+    a.views = d_views;
+    a.n_views = n;
+    a.width = s.width;
+    a.height = s.height;
+    a.packet_w = cfg.packet_w;
+    a.packet_h = cfg.packet_h;
+    a.tiles_x = (s.width + cfg.packet_w - 1) / cfg.packet_w;
+    a.tiles_y = (s.height + cfg.packet_h - 1) / cfg.packet_h;
+    a.total_items = static_cast<long long>(n) * a.tiles_x * a.tiles_y;
+    a.out = out;
+    a.samples = samples;
+    a.queue = queue;
+    a.error_word = err_word;
+    a.persistent = cfg.persistent;
+}
+
+// Renders n views whose records are already set up on the host, without a
+// cached graph: stream-ordered scratch for the view table and queue counter.
+int render_direct(Ctx &ctx, const Volume &vol, const std::vector<ViewDev> &hv, const gbd_image_spec &spec,
+                  const LaunchCfg &cfg, cudaStream_t st)
+{
+    const int n = static_cast<int>(hv.size());
+    const size_t vbytes = sizeof(ViewDev) * hv.size();
+    const size_t pix = static_cast<size_t>(spec.width) * spec.height * n;
+    char *scratch = nullptr;
+    const size_t img_off = (vbytes + 255) / 256 * 256 + 256;
+    const size_t total = img_off + (spec.out_on_host ? pix * sizeof(float) : 0);
+    cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&scratch), total, st);
+    if (e != cudaSuccess) return cuda_fail(e, "render scratch");
+    ViewDev *d_views = reinterpret_cast<ViewDev *>(scratch);
+    int *queue = reinterpret_cast<int *>(scratch + img_off - 256);
+    float *dev_out = spec.out_on_host ? reinterpret_cast<float *>(scratch + img_off) : spec.out;
+    e = cudaMemcpyAsync(d_views, hv.data(), vbytes, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(queue, 0, 256, st);
+    MarchArgs a;
+    fill_args(a, vol, d_views, n, spec, dev_out, spec.out_on_host ? nullptr : spec.samples, queue, cfg, ctx.err_word);
+    if (e == cudaSuccess) e = launch_march(a, cfg, ctx.num_sms, st);
+    if (e == cudaSuccess && spec.out_on_host)
+        e = cudaMemcpyAsync(spec.out, dev_out, pix * sizeof(float), cudaMemcpyDeviceToHost, st);
+    cudaError_t ef = cudaFreeAsync(scratch, st);
+    if (e != cudaSuccess) return cuda_fail(e, "render launch");
+    if (ef != cudaSuccess) return cuda_fail(ef, "render scratch free");
+    set_launch_count(1);
+    return GBD_OK;
+}
+
+// ------------------------------------------------------------------ graphs
+struct GraphKey {
+    gbd_volume vol;
+    int n, width, height;
+    const void *out;
+    const void *samples;
+    int out_on_host;
+    LaunchCfg cfg;
+    bool operator<(const GraphKey &o) const
+    {
+        return std::memcmp(this, &o, sizeof(GraphKey)) < 0;
+    }
+};
+
+struct GraphEntry {
+    cudaGraphExec_t exec = nullptr;
+    char *d_scratch = nullptr;  // view table + queue counter (+ image when out_on_host)
+    ViewDev *h_views = nullptr; // pinned staging of the view table
+    cudaEvent_t done = nullptr;
+    bool launched = false;
+    ~GraphEntry()
+    {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (done) cudaEventDestroy(done);
+        if (h_views) cudaFreeHost(h_views);
+        if (d_scratch) cudaFree(d_scratch);
+    }
+};
+
+// Bounded: the least recently used graph is dropped beyond kMaxGraphs.
+constexpr size_t kMaxGraphs = 64;
+
+struct GraphCache {
+    std::map<GraphKey, std::unique_ptr<GraphEntry>> entries;
+    std::map<GraphKey, uint64_t> last_use;
+    uint64_t clock = 0;
+};
+
+void destroy_graph_cache(GraphCache *g) { delete g; }
+
+void drop_graphs_for(Ctx &ctx, gbd_volume vol)
+{
+    if (!ctx.graphs) return;
+    auto &m = ctx.graphs->entries;
+    for (auto it = m.begin(); it != m.end();) {
+        if (it->first.vol == vol) {
+            if (it->second->launched) cudaEventSynchronize(it->second->done);
+            ctx.graphs->last_use.erase(it->first);
+            it = m.erase(it);
+        } else {
+            ++it;
+        }
+    }
+}
+
+static int build_graph(Ctx &ctx, const Volume &vol, const GraphKey &key, const gbd_image_spec &spec,
+                       GraphEntry &g)
+{
+    const int n = key.n;
+    const size_t vbytes = sizeof(ViewDev) * n;
+    const size_t img_off = (vbytes + 255) / 256 * 256 + 256;
+    const size_t pix = static_cast<size_t>(spec.width) * spec.height * n;
+    const size_t total = img_off + (spec.out_on_host ? pix * sizeof(float) : 0);
+    cudaError_t e = cudaMalloc(reinterpret_cast<void **>(&g.d_scratch), total);
+    if (e != cudaSuccess) return cuda_fail(e, "batch scratch");
+    e = cudaMallocHost(reinterpret_cast<void **>(&g.h_views), vbytes);
+    if (e != cudaSuccess) return cuda_fail(e, "batch pinned staging");
+    e = cudaEventCreateWithFlags(&g.done, cudaEventDisableTiming);
+    if (e != cudaSuccess) return cuda_fail(e, "batch event");
+    ViewDev *d_views = reinterpret_cast<ViewDev *>(g.d_scratch);
+    int *queue = reinterpret_cast<int *>(g.d_scratch + img_off - 256);
+    float *dev_out = spec.out_on_host ? reinterpret_cast<float *>(g.d_scratch + img_off) : spec.out;
+
+    cudaStream_t cap = ctx.capture_stream;
+    e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return cuda_fail(e, "begin capture");
+    cudaError_t e2 = cudaMemcpyAsync(d_views, g.h_views, vbytes, cudaMemcpyHostToDevice, cap);
+    if (e2 == cudaSuccess) e2 = cudaMemsetAsync(queue, 0, 256, cap);
+    MarchArgs a;
+    fill_args(a, vol, d_views, n, spec, dev_out, spec.out_on_host ? nullptr : spec.samples, queue, key.cfg,
+              ctx.err_word);
+    if (e2 == cudaSuccess) e2 = launch_march(a, key.cfg, ctx.num_sms, cap);
+    if (e2 == cudaSuccess && spec.out_on_host)
+        e2 = cudaMemcpyAsync(spec.out, dev_out, pix * sizeof(float), cudaMemcpyDeviceToHost, cap);
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamEndCapture(cap, &graph);
+    if (e2 != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        return cuda_fail(e2, "capture batch");
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "end capture");
+    e = cudaGraphInstantiate(&g.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return cuda_fail(e, "instantiate batch graph");
+    return GBD_OK;
+}
+
+int render_graph(Ctx &ctx, const Volume &vol, gbd_volume vid, const std::vector<ViewDev> &hv,
+                 const gbd_image_spec &spec, const LaunchCfg &cfg, cudaStream_t st)
+{
+    if (!ctx.graphs) ctx.graphs = new GraphCache();
+    GraphKey key;
+    std::memset(&key, 0, sizeof(key));
+    key.vol = vid;
+    key.n = static_cast<int>(hv.size());
+    key.width = spec.width;
+    key.height = spec.height;
+    key.out = spec.out;
+    key.samples = spec.out_on_host ? nullptr : spec.samples;
+    key.out_on_host = spec.out_on_host;
+    key.cfg = cfg;
+    GraphCache &gc = *ctx.graphs;
+    if (gc.entries.find(key) == gc.entries.end() && gc.entries.size() >= kMaxGraphs) {
+        auto oldest = std::min_element(gc.last_use.begin(), gc.last_use.end(),
+                                       [](const auto &x, const auto &y) { return x.second < y.second; });
+        auto victim = gc.entries.find(oldest->first);
+        if (victim->second->launched) cudaEventSynchronize(victim->second->done);
+        gc.entries.erase(victim);
+        gc.last_use.erase(oldest);
+    }
+    gc.last_use[key] = ++gc.clock;
+    auto &slot = gc.entries[key];
+    const size_t vbytes = sizeof(ViewDev) * hv.size();
+    if (!slot) {
+        auto g = std::make_unique<GraphEntry>();
+        int rc = build_graph(ctx, vol, key, spec, *g);
+        if (rc != GBD_OK) {
+            gc.entries.erase(key);
+            gc.last_use.erase(key);
+            return rc;
+        }
+        std::memcpy(g->h_views, hv.data(), vbytes);
+        slot = std::move(g);
+    } else if (std::memcmp(slot->h_views, hv.data(), vbytes) != 0) {
+        // The previous replay may still be reading the pinned staging buffer.
+        if (slot->launched) {
+            cudaError_t e = cudaEventSynchronize(slot->done);
+            if (e != cudaSuccess) return cuda_fail(e, "wait for previous batch");
+        }
+        std::memcpy(slot->h_views, hv.data(), vbytes);
+    }
+    cudaError_t e = cudaGraphLaunch(slot->exec, st);
+    if (e != cudaSuccess) return cuda_fail(e, "graph launch");
+    e = cudaEventRecord(slot->done, st);
+    if (e != cudaSuccess) return cuda_fail(e, "graph event");
+    slot->launched = true;
+    set_launch_count(1);
+    return GBD_OK;
+}
+
+}  // namespace gbd
+
+using namespace gbd;
+
+gbd_ctx::~gbd_ctx() = default;
+
+Volume *gbd_ctx::find(gbd_volume id)
+{
+    auto it = volumes.find(id);
+    return it == volumes.end() ? nullptr : it->second.get();
+}
+
+// ====================================================================== C ABI
+extern "C" {
+
+const char *gbd_error_string(int status)
+{
+    switch (status) {
+    case GBD_OK: return "ok";
+    case GBD_ERR_INVALID: return "invalid argument";
+    case GBD_ERR_NOMEM: return "out of memory";
+    case GBD_ERR_BUDGET: return "exceeds the HBM budget";
+    case GBD_ERR_NOTFOUND: return "not found";
+    case GBD_ERR_TIMEOUT: return "timed out";
+    case GBD_ERR_CUDA: return "CUDA error";
+    case GBD_ERR_CANCELLED: return "cancelled";
+    case GBD_ERR_BUSY: return "busy";
+    default: return "unknown status";
+    }
+}
+
+const char *gbd_last_error(void) { return t_last_error.c_str(); }
+
+int32_t gbd_last_launch_count(void) { return t_last_launches; }
+
+int gbd_bounds_violations(gbd_ctx *ctx, int32_t *out)
+{
+    if (!ctx || !out) return fail(GBD_ERR_INVALID, "NULL argument");
+    std::lock_guard<std::mutex> lock(ctx->mu);
+    DeviceGuard guard(ctx->device);
+    cudaError_t e = cudaDeviceSynchronize();
+    int word = 0;
+    if (e == cudaSuccess) e = cudaMemcpy(&word, ctx->err_word, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemset(ctx->err_word, 0, sizeof(int));
+    if (e != cudaSuccess) return cuda_fail(e, "bounds word");
+    *out = word;
+    return GBD_OK;
+}
+
+int gbd_create(gbd_ctx **out, int32_t device, uint64_t hbm_budget_bytes)
+{
+    if (!out) return fail(GBD_ERR_INVALID, "out is NULL");
+    *out = nullptr;
+    int ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDeviceCount");
+    if (device < 0 || device >= ndev) return fail(GBD_ERR_INVALID, "device %d out of range (%d devices)", device, ndev);
+    DeviceGuard guard(device);
+    auto ctx = std::make_unique<gbd_ctx>();
+    ctx->device = device;
+    e = cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device);
+    if (e != cudaSuccess) return cuda_fail(e, "multiprocessor count");
+    size_t free_b = 0, total_b = 0;
+    e = cudaMemGetInfo(&free_b, &total_b);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemGetInfo");
+    ctx->budget = hbm_budget_bytes ? hbm_budget_bytes : static_cast<uint64_t>(0.9 * static_cast<double>(free_b));
+    e = cudaStreamCreateWithFlags(&ctx->load_stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return cuda_fail(e, "load stream");
+    e = cudaStreamCreateWithFlags(&ctx->capture_stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return cuda_fail(e, "capture stream");
+    e = cudaMalloc(reinterpret_cast<void **>(&ctx->err_word), 256);
+    if (e != cudaSuccess) return cuda_fail(e, "error word");
+    e = cudaMemset(ctx->err_word, 0, 256);
+    if (e != cudaSuccess) return cuda_fail(e, "error word clear");
+    load_tune_file(*ctx);
+    *out = ctx.release();
+    return GBD_OK;
+}
+
+int gbd_destroy(gbd_ctx *ctx)
+{
+    if (!ctx) return GBD_OK;
+    {
+        DeviceGuard guard(ctx->device);
+        serve_shutdown(*ctx);
+        cudaDeviceSynchronize();
+        destroy_graph_cache(ctx->graphs);
+        ctx->graphs = nullptr;
+        for (auto &kv : ctx->volumes) {
+            if (kv.second->rec) cudaFree(kv.second->rec);
+            if (kv.second->axis_off) cudaFree(kv.second->axis_off);
+        }
+        ctx->volumes.clear();
+        if (ctx->err_word) cudaFree(ctx->err_word);
+        if (ctx->load_stream) cudaStreamDestroy(ctx->load_stream);
+        if (ctx->capture_stream) cudaStreamDestroy(ctx->capture_stream);
+    }
+    delete ctx;
+    return GBD_OK;
+}
+
+int gbd_load_snapshots(gbd_ctx *ctx, const gbd_grid *grid, const gbd_fields *f, gbd_volume *out)
+{
+    if (!ctx || !grid || !f || !out) return fail(GBD_ERR_INVALID, "NULL argument");
+    *out = 0;
+    const gbd_grid &g = *grid;
+    for (int i = 0; i < 3; ++i) {
+        if (g.n[i] < 1 || g.n[i] > kMaxAxis) return fail(GBD_ERR_INVALID, "grid: n[%d] must be in [1, %d]", i, kMaxAxis);
+        if (!(g.dx[i] > 0.0) || !std::isfinite(g.dx[i]) || !std::isfinite(g.origin[i]))
+            return fail(GBD_ERR_INVALID, "grid: dx must be positive and origin finite");
+    }
+    if (g.n_epochs < 1 || g.n_epochs > 1000000) return fail(GBD_ERR_INVALID, "grid: n_epochs must be >= 1");
+    if (!(g.dt > 0.0) || !std::isfinite(g.dt) || !std::isfinite(g.t0))
+        return fail(GBD_ERR_INVALID, "grid: dt must be positive and t0 finite");
+    if (!f->j || !f->vel) return fail(GBD_ERR_INVALID, "fields: NULL array");
+    if (f->dtype_in != GBD_IN_F64 && f->dtype_in != GBD_IN_F32) return fail(GBD_ERR_INVALID, "fields: bad dtype_in");
+    if (f->store != GBD_STORE_F32 && f->store != GBD_STORE_BF16_F16U) return fail(GBD_ERR_INVALID, "fields: bad store");
+    int B = f->brick ? f->brick : 8;
+    int S = f->super_brick ? f->super_brick : 4;
+    if (B != 1 && B != 2 && B != 4 && B != 8) return fail(GBD_ERR_INVALID, "fields: brick must be 1, 2, 4 or 8");
+    if (S != 1 && S != 2 && S != 4) return fail(GBD_ERR_INVALID, "fields: super_brick must be 1, 2 or 4");
+
+    std::lock_guard<std::mutex> lock(ctx->mu);
+    DeviceGuard guard(ctx->device);
+    auto vol = std::make_unique<Volume>();
+    vol->grid = g;
+    vol->store = f->store;
+    vol->brick = B;
+    vol->super_brick = S;
+    std::vector<int32_t> tab;
+    if (!build_layout(g.n, B, S, tab, vol->epoch_stride))
+        return fail(GBD_ERR_INVALID, "grid too large: one epoch exceeds 2^31 records");
+    const size_t rec_bytes = f->store == GBD_STORE_F32 ? 16 : 8;
+    const size_t bytes = rec_bytes * static_cast<size_t>(vol->epoch_stride) * g.n_epochs;
+    const size_t tab_bytes = tab.size() * sizeof(int32_t);
+    if (ctx->used + bytes + tab_bytes > ctx->budget)
+        return fail(GBD_ERR_BUDGET, "volume needs %zu bytes, %llu of %llu budget in use", bytes + tab_bytes,
+                    static_cast<unsigned long long>(ctx->used), static_cast<unsigned long long>(ctx->budget));
+    if (fault_injected("alloc")) return fail(GBD_ERR_NOMEM, "injected allocation failure");
+    cudaError_t e = cudaMalloc(&vol->rec, bytes);
+    if (e != cudaSuccess) return cuda_fail(e, "volume allocation");
+    auto cleanup = [&]() {
+        cudaFree(vol->rec);
+        vol->rec = nullptr;
+        if (vol->axis_off) cudaFree(vol->axis_off);
+        vol->axis_off = nullptr;
+    };
+    e = cudaMalloc(reinterpret_cast<void **>(&vol->axis_off), tab_bytes);
+    if (e != cudaSuccess) { cleanup(); return cuda_fail(e, "layout table allocation"); }
+    cudaStream_t st = ctx->load_stream;
+    e = cudaMemcpyAsync(vol->axis_off, tab.data(), tab_bytes, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(vol->rec, 0, bytes, st);
+    if (e != cudaSuccess) { cleanup(); return cuda_fail(e, "volume init"); }
+
+    const size_t esz = f->dtype_in == GBD_IN_F64 ? 8 : 4;
+    const size_t ncell = static_cast<size_t>(g.n[0]) * g.n[1] * g.n[2];
+    char *stage = nullptr;
+    int *bad = nullptr;
+    e = cudaMallocAsync(reinterpret_cast<void **>(&bad), 256, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(bad, 0, 256, st);
+    if (e == cudaSuccess && !f->on_device) e = cudaMallocAsync(reinterpret_cast<void **>(&stage), ncell * esz * 4, st);
+    for (int m = 0; m < g.n_epochs && e == cudaSuccess; ++m) {
+        const char *jsrc = static_cast<const char *>(f->j) + m * ncell * esz;
+        const char *vsrc = static_cast<const char *>(f->vel) + m * ncell * esz * 3;
+        PackArgs pa;
+        std::memset(&pa, 0, sizeof(pa));
+        if (f->on_device) {
+            pa.j = jsrc;
+            pa.vel = vsrc;
+        } else {
+            e = cudaMemcpyAsync(stage, jsrc, ncell * esz, cudaMemcpyHostToDevice, st);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(stage + ncell * esz, vsrc, ncell * esz * 3, cudaMemcpyHostToDevice, st);
+            pa.j = stage;
+            pa.vel = stage + ncell * esz;
+        }
+        pa.dtype_in = f->dtype_in;
+        pa.store = f->store;
+        for (int i = 0; i < 3; ++i) pa.n[i] = g.n[i];
+        pa.axis_off = vol->axis_off;
+        pa.dst = static_cast<char *>(vol->rec) + static_cast<size_t>(m) * vol->epoch_stride * rec_bytes;
+        pa.bad = bad;
+        if (e == cudaSuccess) e = launch_pack(pa, st);
+        // The host staging buffer is reused for the next epoch only after
+        // this epoch's pack has consumed it.
+        if (e == cudaSuccess && !f->on_device) e = cudaStreamSynchronize(st);
+    }
+    int h_bad = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h_bad, bad, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (stage) cudaFreeAsync(stage, st);
+    if (bad) cudaFreeAsync(bad, st);
+    cudaError_t es = cudaStreamSynchronize(st);
+    if (e == cudaSuccess) e = es;
+    if (e != cudaSuccess) { cleanup(); return cuda_fail(e, "volume pack"); }
+    if (h_bad) {
+        cleanup();
+        return fail(GBD_ERR_INVALID, "fields: negative or non-finite j', non-finite beta, or |beta| >= 1 "
+                                     "(float32 storage needs |beta|^2 <= 1 - 2^-20)");
+    }
+    vol->bytes = bytes + tab_bytes;
+    ctx->used += vol->bytes;
+    const gbd_volume id = ++ctx->next_id;
+    ctx->volumes[id] = std::move(vol);
+    *out = id;
+    return GBD_OK;
+}
+
+int gbd_unload(gbd_ctx *ctx, gbd_volume vid)
+{
+    if (!ctx) return fail(GBD_ERR_INVALID, "ctx is NULL");
+    std::lock_guard<std::mutex> lock(ctx->mu);
+    Volume *v = ctx->find(vid);
+    if (!v) return fail(GBD_ERR_NOTFOUND, "unknown volume %llu", static_cast<unsigned long long>(vid));
+    if (v->pinned_by_requests > 0) return fail(GBD_ERR_BUSY, "volume has %d queued requests", v->pinned_by_requests);
+    DeviceGuard guard(ctx->device);
+    drop_graphs_for(*ctx, vid);
+    // Work already enqueued on other streams may still read the volume.
+    cudaDeviceSynchronize();
+    cudaFree(v->rec);
+    cudaFree(v->axis_off);
+    ctx->used -= v->bytes;
+    ctx->volumes.erase(vid);
+    return GBD_OK;
+}
+
+int gbd_volume_info(gbd_ctx *ctx, gbd_volume vid, gbd_volume_desc *out)
+{
+    if (!ctx || !out) return fail(GBD_ERR_INVALID, "NULL argument");
+    std::lock_guard<std::mutex> lock(ctx->mu);
+    Volume *v = ctx->find(vid);
+    if (!v) return fail(GBD_ERR_NOTFOUND, "unknown volume %llu", static_cast<unsigned long long>(vid));
+    out->grid = v->grid;
+    out->store = v->store;
+    out->brick = v->brick;
+    out->super_brick = v->super_brick;
+    out->bytes = v->bytes;
+    out->record_bytes = v->store == GBD_STORE_F32 ? 16 : 8;
+    return GBD_OK;
+}
+
+int gbd_render(gbd_ctx *ctx, gbd_volume vid, const gbd_view *view, const gbd_image_spec *spec,
+               const gbd_launch *launch, void *stream)
+{
+    if (!ctx || !view) return fail(GBD_ERR_INVALID, "NULL argument");
+    int rc = check_spec(spec);
+    if (rc) return rc;
+    LaunchCfg cfg = resolve_launch(launch);
+    if ((rc = check_launch(cfg))) return rc;
+    std::lock_guard<std::mutex> lock(ctx->mu);
+    Volume *vol = ctx->find(vid);
+    if (!vol) return fail(GBD_ERR_NOTFOUND, "unknown volume %llu", static_cast<unsigned long long>(vid));
+    if (!launch) lookup_tuned(*ctx, tune_key(*vol, spec->width, spec->height, 1, view->flags), cfg);
+    DeviceGuard guard(ctx->device);
+    std::vector<ViewDev> hv(1);
+    if ((rc = make_view(*vol, *view, spec->width, spec->height, spec->fov_u, spec->fov_v, hv[0]))) return rc;
+    return render_direct(*ctx, *vol, hv, *spec, cfg, static_cast<cudaStream_t>(stream));
+}
+
+int gbd_render_batch(gbd_ctx *ctx, gbd_volume vid, const gbd_view *views, int32_t n, const gbd_image_spec *spec,
+                     const gbd_launch *launch, void *stream)
+{
+    if (!ctx || !views) return fail(GBD_ERR_INVALID, "NULL argument");
+    if (n < 1 || n > (1 << 20)) return fail(GBD_ERR_INVALID, "batch size must be in [1, 2^20]");
+    int rc = check_spec(spec);
+    if (rc) return rc;
+    LaunchCfg cfg = resolve_launch(launch);
+    if ((rc = check_launch(cfg))) return rc;
+    std::lock_guard<std::mutex> lock(ctx->mu);
+    Volume *vol = ctx->find(vid);
+    if (!vol) return fail(GBD_ERR_NOTFOUND, "unknown volume %llu", static_cast<unsigned long long>(vid));
+    if (!launch) lookup_tuned(*ctx, tune_key(*vol, spec->width, spec->height, n, views[0].flags), cfg);
+    DeviceGuard guard(ctx->device);
+    std::vector<ViewDev> hv(static_cast<size_t>(n));
+    for (int k = 0; k < n; ++k)
+        if ((rc = make_view(*vol, views[k], spec->width, spec->height, spec->fov_u, spec->fov_v, hv[k]))) return rc;
+    if (graphs_enabled()) return render_graph(*ctx, *vol, vid, hv, *spec, cfg, static_cast<cudaStream_t>(stream));
+    return render_direct(*ctx, *vol, hv, *spec, cfg, static_cast<cudaStream_t>(stream));
+}
+
+}  // extern "C"

@@ -1,0 +1,114 @@
+// runtime.h -- host-side state of a context (not part of the public ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <vector>
+
+#include "gbd_internal.h"
+
+namespace gbd {
+
+// A packed, device-resident snapshot series.
+struct Volume {
+    gbd_grid grid{};
+    int store = GBD_STORE_F32;
+    int brick = 8, super_brick = 4;
+    void *rec = nullptr;             // records, epoch after epoch
+    int32_t *axis_off = nullptr;     // per-axis offset tables (n_x + n_y + n_z)
+    long long epoch_stride = 0;      // records per epoch
+    uint64_t bytes = 0;              // device bytes charged to the budget
+    int pinned_by_requests = 0;      // queued serving requests using it
+};
+
+struct GraphCache;
+struct Server;
+
+// Autotuning class of a render: results are cached per key.
+struct TuneKey {
+    int n[3];
+    int M, store, width, height, n_views, lookback;
+    bool operator<(const TuneKey &o) const { return std::memcmp(this, &o, sizeof(TuneKey)) < 0; }
+};
+
+struct TuneEntry {
+    LaunchCfg cfg{8, 4, 8, 2, 1};
+    int brick = 8, super_brick = 4;
+    float ms = 0.f;
+};
+
+}  // namespace gbd
+
+struct gbd_ctx {
+    int device = 0;
+    int num_sms = 0;
+    uint64_t budget = 0;
+    uint64_t used = 0;
+    std::mutex mu;
+    std::map<gbd_volume, std::unique_ptr<gbd::Volume>> volumes;
+    gbd_volume next_id = 0;
+    cudaStream_t load_stream = nullptr;
+    cudaStream_t capture_stream = nullptr;
+    int *err_word = nullptr;          // bounds-check word of checked builds
+    gbd::GraphCache *graphs = nullptr;
+    gbd::Server *server = nullptr;
+    std::map<gbd::TuneKey, gbd::TuneEntry> tuned;
+    ~gbd_ctx();
+    gbd::Volume *find(gbd_volume id);
+};
+
+namespace gbd {
+
+using Ctx = ::gbd_ctx;
+
+// Errors: record a message for gbd_last_error() and return the code.
+int fail(int code, const char *fmt, ...);
+int cuda_fail(cudaError_t e, const char *what);
+void set_launch_count(int32_t n);
+
+// Restores the caller's current device on scope exit.
+class DeviceGuard {
+  public:
+    explicit DeviceGuard(int dev);
+    ~DeviceGuard();
+    DeviceGuard(const DeviceGuard &) = delete;
+    DeviceGuard &operator=(const DeviceGuard &) = delete;
+
+  private:
+    int prev_ = 0;
+};
+
+// Settings read from the environment once (runtime.cpp).
+bool graphs_enabled();                 // GBD_GRAPHS=0 disables graph replay of batches
+bool fault_injected(const char *site); // GBD_FAULT=alloc:N,admit:N fails the N-th call at a site
+void reset_fault_counters();
+
+// View and launch helpers (api.cpp).
+int make_view(const Volume &vol, const gbd_view &v, int width, int height, double fov_u, double fov_v, ViewDev &out);
+VolDev vol_dev(const Volume &v);
+LaunchCfg resolve_launch(const gbd_launch *l);
+int check_launch(const LaunchCfg &c);
+void fill_args(MarchArgs &a, const Volume &vol, const ViewDev *d_views, int n, const gbd_image_spec &s,
+               float *out, uint32_t *samples, int *queue, const LaunchCfg &cfg, int *err_word);
+bool build_layout(const int n[3], int B, int S, std::vector<int32_t> &tab, long long &epoch_stride);
+void destroy_graph_cache(GraphCache *g);
+
+void drop_graphs_for(Ctx &ctx, gbd_volume vol);
+int render_direct(Ctx &ctx, const Volume &vol, const std::vector<ViewDev> &hv, const gbd_image_spec &spec,
+                  const LaunchCfg &cfg, cudaStream_t st);
+
+// Autotuning (tune.cpp).
+TuneKey tune_key(const Volume &vol, int width, int height, int n_views, uint32_t flags);
+bool lookup_tuned(Ctx &ctx, const TuneKey &k, LaunchCfg &cfg);
+void load_tune_file(Ctx &ctx);
+int relayout_volume(Ctx &ctx, Volume &vol, gbd_volume vid, int B, int S);
+
+// Serving (serve.cpp).
+void serve_shutdown(Ctx &ctx);
+
+}  // namespace gbd

@@ -1,0 +1,297 @@
+// tune.cpp -- autotuner of the march launch and of the volume layout.
+//
+// For one (grid, storage, epochs, image size, batch size, lookback) class the
+// tuner times every candidate launch configuration (warp packet shape, warps
+// per CTA, cells gathered ahead per lane) with CUDA events and, on request,
+// every candidate brick / super-brick layout by re-packing the resident volume
+// on the device.  The winner is cached in the context and used by render calls
+// that pass no launch configuration; with GBD_TUNE_CACHE=<file> results are
+// also appended to, and read back from, a text file.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "runtime.h"
+
+namespace gbd {
+
+TuneKey tune_key(const Volume &vol, int width, int height, int n_views, uint32_t flags)
+{
+    TuneKey k;
+    std::memset(&k, 0, sizeof(k));
+    for (int i = 0; i < 3; ++i) k.n[i] = vol.grid.n[i];
+    k.M = vol.grid.n_epochs;
+    k.store = vol.store;
+    k.width = width;
+    k.height = height;
+    k.n_views = n_views;
+    k.lookback = (flags & GBD_LOOKBACK) ? 1 : 0;
+    return k;
+}
+
+namespace {
+
+std::mutex g_file_mu;
+
+std::string key_text(const TuneKey &k)
+{
+    char buf[160];
+    std::snprintf(buf, sizeof(buf), "%d %d %d %d %d %d %d %d %d", k.n[0], k.n[1], k.n[2], k.M, k.store, k.width,
+                  k.height, k.n_views, k.lookback);
+    return buf;
+}
+
+void append_cache_file(const TuneKey &k, const TuneEntry &e)
+{
+    const char *path = std::getenv("GBD_TUNE_CACHE");
+    if (!path || !*path) return;
+    std::lock_guard<std::mutex> lock(g_file_mu);
+    FILE *f = std::fopen(path, "a");
+    if (!f) return;
+    std::fprintf(f, "%s -> %d %d %d %d %d %d %d %.6f\n", key_text(k).c_str(), e.cfg.packet_w, e.cfg.packet_h,
+                 e.cfg.cta_warps, e.cfg.depth, e.cfg.persistent, e.brick, e.super_brick, e.ms);
+    std::fclose(f);
+}
+
+// Renders once with the given configuration; returns the elapsed time in ms
+// (median of `reps` timed repetitions after one warm-up).
+int time_config(Ctx &ctx, const Volume &vol, const std::vector<ViewDev> &hv, const gbd_image_spec &spec,
+                const LaunchCfg &cfg, cudaStream_t st, int reps, float &ms_out)
+{
+    const int n = static_cast<int>(hv.size());
+    char *scratch = nullptr;
+    const size_t vbytes = sizeof(ViewDev) * hv.size();
+    const size_t qoff = (vbytes + 255) / 256 * 256;
+    cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&scratch), qoff + 256, st);
+    if (e != cudaSuccess) return cuda_fail(e, "tune scratch");
+    e = cudaMemcpyAsync(scratch, hv.data(), vbytes, cudaMemcpyHostToDevice, st);
+    cudaEvent_t a = nullptr, b = nullptr;
+    if (e == cudaSuccess) e = cudaEventCreate(&a);
+    if (e == cudaSuccess) e = cudaEventCreate(&b);
+    std::vector<float> times;
+    for (int r = 0; r <= reps && e == cudaSuccess; ++r) {
+        MarchArgs args;
+        fill_args(args, vol, reinterpret_cast<ViewDev *>(scratch), n, spec, spec.out, nullptr,
+                  reinterpret_cast<int *>(scratch + qoff), cfg, ctx.err_word);
+        e = cudaMemsetAsync(scratch + qoff, 0, 256, st);
+        if (e == cudaSuccess) e = cudaEventRecord(a, st);
+        if (e == cudaSuccess) e = launch_march(args, cfg, ctx.num_sms, st);
+        if (e == cudaSuccess) e = cudaEventRecord(b, st);
+        if (e == cudaSuccess) e = cudaEventSynchronize(b);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+        if (r > 0) times.push_back(ms);
+    }
+    if (a) cudaEventDestroy(a);
+    if (b) cudaEventDestroy(b);
+    cudaFreeAsync(scratch, st);
+    if (e != cudaSuccess) return cuda_fail(e, "tune launch");
+    std::sort(times.begin(), times.end());
+    ms_out = times[times.size() / 2];
+    return GBD_OK;
+}
+
+}  // namespace
+
+// Re-packs a volume into another brick / super-brick layout on the device.
+// The handle keeps its identity; cached graphs of the volume are dropped
+// because their kernel parameters point at the old records.
+int relayout_volume(Ctx &ctx, Volume &vol, gbd_volume vid, int B, int S)
+{
+    if (B == vol.brick && S == vol.super_brick) return GBD_OK;
+    std::vector<int32_t> tab;
+    long long stride = 0;
+    if (!build_layout(vol.grid.n, B, S, tab, stride)) return fail(GBD_ERR_INVALID, "layout too large");
+    const size_t rec_bytes = vol.store == GBD_STORE_F32 ? 16 : 8;
+    const size_t bytes = rec_bytes * static_cast<size_t>(stride) * vol.grid.n_epochs;
+    const size_t tab_bytes = tab.size() * sizeof(int32_t);
+    if (ctx.used + bytes + tab_bytes > ctx.budget)
+        return fail(GBD_ERR_BUDGET, "re-layout needs %zu more bytes", bytes + tab_bytes);
+    void *rec = nullptr;
+    int32_t *off = nullptr;
+    cudaError_t e = cudaMalloc(&rec, bytes);
+    if (e != cudaSuccess) return cuda_fail(e, "re-layout allocation");
+    e = cudaMalloc(reinterpret_cast<void **>(&off), tab_bytes);
+    if (e != cudaSuccess) {
+        cudaFree(rec);
+        return cuda_fail(e, "re-layout table allocation");
+    }
+    cudaStream_t st = ctx.load_stream;
+    e = cudaMemcpyAsync(off, tab.data(), tab_bytes, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(rec, 0, bytes, st);
+    for (int m = 0; m < vol.grid.n_epochs && e == cudaSuccess; ++m) {
+        RelayoutArgs ra;
+        std::memset(&ra, 0, sizeof(ra));
+        ra.src = static_cast<const char *>(vol.rec) + static_cast<size_t>(m) * vol.epoch_stride * rec_bytes;
+        ra.dst = static_cast<char *>(rec) + static_cast<size_t>(m) * stride * rec_bytes;
+        ra.src_off = vol.axis_off;
+        ra.dst_off = off;
+        for (int i = 0; i < 3; ++i) ra.n[i] = vol.grid.n[i];
+        ra.record_bytes = static_cast<int>(rec_bytes);
+        e = launch_relayout(ra, st);
+    }
+    cudaError_t es = cudaStreamSynchronize(st);
+    if (e == cudaSuccess) e = es;
+    if (e != cudaSuccess) {
+        cudaFree(rec);
+        cudaFree(off);
+        return cuda_fail(e, "re-layout");
+    }
+    drop_graphs_for(ctx, vid);
+    cudaDeviceSynchronize();  // work on other streams may still read the old records
+    cudaFree(vol.rec);
+    cudaFree(vol.axis_off);
+    ctx.used -= vol.bytes;
+    vol.rec = rec;
+    vol.axis_off = off;
+    vol.epoch_stride = stride;
+    vol.brick = B;
+    vol.super_brick = S;
+    vol.bytes = bytes + tab_bytes;
+    ctx.used += vol.bytes;
+    return GBD_OK;
+}
+
+bool lookup_tuned(Ctx &ctx, const TuneKey &k, LaunchCfg &cfg)
+{
+    auto it = ctx.tuned.find(k);
+    if (it == ctx.tuned.end()) return false;
+    cfg = it->second.cfg;
+    return true;
+}
+
+void load_tune_file(Ctx &ctx)
+{
+    const char *path = std::getenv("GBD_TUNE_CACHE");
+    if (!path || !*path) return;
+    std::lock_guard<std::mutex> lock(g_file_mu);
+    FILE *f = std::fopen(path, "r");
+    if (!f) return;
+    char line[256];
+    while (std::fgets(line, sizeof(line), f)) {
+        TuneKey k;
+        std::memset(&k, 0, sizeof(k));
+        TuneEntry e;
+        if (std::sscanf(line, "%d %d %d %d %d %d %d %d %d -> %d %d %d %d %d %d %d %f", &k.n[0], &k.n[1], &k.n[2],
+                        &k.M, &k.store, &k.width, &k.height, &k.n_views, &k.lookback, &e.cfg.packet_w,
+                        &e.cfg.packet_h, &e.cfg.cta_warps, &e.cfg.depth, &e.cfg.persistent, &e.brick,
+                        &e.super_brick, &e.ms) == 17 &&
+            check_launch(e.cfg) == GBD_OK)
+            ctx.tuned[k] = e;  // later lines win
+    }
+    std::fclose(f);
+}
+
+}  // namespace gbd
+
+using namespace gbd;
+
+extern "C" {
+
+int gbd_relayout(gbd_ctx *ctx, gbd_volume vid, int32_t brick, int32_t super_brick)
+{
+    if (!ctx) return fail(GBD_ERR_INVALID, "ctx is NULL");
+    if (brick != 1 && brick != 2 && brick != 4 && brick != 8) return fail(GBD_ERR_INVALID, "brick must be 1, 2, 4 or 8");
+    if (super_brick != 1 && super_brick != 2 && super_brick != 4)
+        return fail(GBD_ERR_INVALID, "super_brick must be 1, 2 or 4");
+    std::lock_guard<std::mutex> lock(ctx->mu);
+    Volume *v = ctx->find(vid);
+    if (!v) return fail(GBD_ERR_NOTFOUND, "unknown volume %llu", static_cast<unsigned long long>(vid));
+    if (v->pinned_by_requests > 0) return fail(GBD_ERR_BUSY, "volume has queued requests");
+    DeviceGuard guard(ctx->device);
+    return relayout_volume(*ctx, *v, vid, brick, super_brick);
+}
+
+int gbd_tune(gbd_ctx *ctx, gbd_volume vid, const gbd_view *views, int32_t n, const gbd_image_spec *spec,
+             uint32_t what, void *stream, gbd_tune_result *out)
+{
+    if (!ctx || !views || !spec || !out) return fail(GBD_ERR_INVALID, "NULL argument");
+    if (n < 1 || n > (1 << 20)) return fail(GBD_ERR_INVALID, "batch size must be in [1, 2^20]");
+    if (!spec->out || spec->out_on_host) return fail(GBD_ERR_INVALID, "tuning needs a device output buffer");
+    if ((what & ~(GBD_TUNE_LAUNCH | GBD_TUNE_LAYOUT)) != 0u || what == 0u)
+        return fail(GBD_ERR_INVALID, "what must combine GBD_TUNE_LAUNCH and GBD_TUNE_LAYOUT");
+    std::lock_guard<std::mutex> lock(ctx->mu);
+    Volume *vol = ctx->find(vid);
+    if (!vol) return fail(GBD_ERR_NOTFOUND, "unknown volume %llu", static_cast<unsigned long long>(vid));
+    if ((what & GBD_TUNE_LAYOUT) && vol->pinned_by_requests > 0) return fail(GBD_ERR_BUSY, "volume has queued requests");
+    DeviceGuard guard(ctx->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    std::vector<ViewDev> hv(static_cast<size_t>(n));
+    int rc;
+    for (int k = 0; k < n; ++k)
+        if ((rc = make_view(*vol, views[k], spec->width, spec->height, spec->fov_u, spec->fov_v, hv[k]))) return rc;
+
+    LaunchCfg best{8, 4, 8, 2, 1};
+    float best_ms = 0.f;
+    int tried = 0;
+    if ((rc = time_config(*ctx, *vol, hv, *spec, best, st, 3, best_ms))) return rc;
+    ++tried;
+    if (what & GBD_TUNE_LAUNCH) {
+        const int packets[3][2] = {{8, 4}, {4, 8}, {16, 2}};
+        const int warps[2] = {4, 8};
+        const int depths[3] = {1, 2, 4};
+        for (const auto &pk : packets)
+            for (int w : warps)
+                for (int d : depths) {
+                    LaunchCfg c{pk[0], pk[1], w, d, 1};
+                    float ms = 0.f;
+                    if ((rc = time_config(*ctx, *vol, hv, *spec, c, st, 3, ms))) return rc;
+                    ++tried;
+                    if (ms < best_ms) {
+                        best_ms = ms;
+                        best = c;
+                    }
+                }
+        LaunchCfg flat{8, 4, 8, 2, 0};
+        float ms = 0.f;
+        if ((rc = time_config(*ctx, *vol, hv, *spec, flat, st, 3, ms))) return rc;
+        ++tried;
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = flat;
+        }
+    }
+    if (what & GBD_TUNE_LAYOUT) {
+        const int layouts[6][2] = {{8, 4}, {8, 2}, {8, 1}, {4, 4}, {4, 2}, {1, 1}};
+        int bestB = vol->brick, bestS = vol->super_brick;
+        for (const auto &ly : layouts) {
+            if ((rc = relayout_volume(*ctx, *vol, vid, ly[0], ly[1]))) return rc;
+            float ms = 0.f;
+            if ((rc = time_config(*ctx, *vol, hv, *spec, best, st, 3, ms))) return rc;
+            ++tried;
+            if (ms < best_ms) {
+                best_ms = ms;
+                bestB = ly[0];
+                bestS = ly[1];
+            }
+        }
+        if ((rc = relayout_volume(*ctx, *vol, vid, bestB, bestS))) return rc;
+    }
+    TuneEntry e;
+    e.cfg = best;
+    e.brick = vol->brick;
+    e.super_brick = vol->super_brick;
+    e.ms = best_ms;
+    const TuneKey key = tune_key(*vol, spec->width, spec->height, n, views[0].flags);
+    ctx->tuned[key] = e;
+    append_cache_file(key, e);
+    out->launch.packet_w = best.packet_w;
+    out->launch.packet_h = best.packet_h;
+    out->launch.cta_warps = best.cta_warps;
+    out->launch.depth = best.depth;
+    out->launch.persistent = best.persistent;
+    out->brick = vol->brick;
+    out->super_brick = vol->super_brick;
+    out->ms = best_ms;
+    out->candidates = tried;
+    return GBD_OK;
+}
+
+}  // extern "C"
