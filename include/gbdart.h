@@ -208,6 +208,30 @@ int gbd_render(gbd_ctx *ctx, gbd_volume vol, const gbd_view *view, const gbd_ima
 int gbd_render_batch(gbd_ctx *ctx, gbd_volume vol, const gbd_view *views, int32_t n,
                      const gbd_image_spec *spec, const gbd_launch *launch, void *stream);
 
+/* Batch rendering without allocation.  The paper has no counterpart: this
+ * entry point exists for callers that cannot let the library allocate device
+ * memory while they render -- applications that hand the whole device to
+ * their own allocator or memory pool up front, and latency-critical loops
+ * where cudaMalloc / cudaFree (which may synchronise the device) are not
+ * acceptable.  It renders like gbd_render_batch, but keeps the view table and
+ * the tile counter of the persistent launch in one fixed-size device array of
+ * the library (about 208 KB, held by every GPU that loads the library until
+ * the process exits) instead of allocating them, and uses no CUDA graph.
+ * Limits and behaviour:
+ *  - at most GBD_NOALLOC_MAX_VIEWS views per call, otherwise GBD_ERR_INVALID;
+ *  - spec->out (and spec->samples, if set) must be device memory;
+ *    out_on_host is rejected with GBD_ERR_INVALID;
+ *  - the first call on a device looks up the array's device address on that
+ *    device (cudaGetSymbolAddress); make that first call before any stream
+ *    capture;
+ *  - every call shares the one array, which keeps the last call's contents
+ *    (the tile counter is cleared by each call): calls whose GPU work overlaps,
+ *    from any context or stream on the same device, race on it, so the caller
+ *    orders them (for example on one stream). */
+#define GBD_NOALLOC_MAX_VIEWS 1024
+int gbd_render_batch_noalloc(gbd_ctx *ctx, gbd_volume vol, const gbd_view *views, int32_t n,
+                             const gbd_image_spec *spec, const gbd_launch *launch, void *stream);
+
 /* Number of kernels the last successful render call of this thread
  * launched (graph replays count their kernels). */
 int32_t gbd_last_launch_count(void);

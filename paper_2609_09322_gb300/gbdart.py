@@ -89,6 +89,8 @@ _SIGNATURES = {
     "gbd_render": ([ctypes.c_void_p, ctypes.c_uint64, ctypes.POINTER(CView), ctypes.POINTER(ImageSpec),
                     ctypes.POINTER(Launch), ctypes.c_void_p], ctypes.c_int),
     "gbd_bounds_violations": ([ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
+    "gbd_render_batch_noalloc": ([ctypes.c_void_p, ctypes.c_uint64, ctypes.POINTER(CView), ctypes.c_int32,
+                                  ctypes.POINTER(ImageSpec), ctypes.POINTER(Launch), ctypes.c_void_p], ctypes.c_int),
     "gbd_tune": ([ctypes.c_void_p, ctypes.c_uint64, ctypes.POINTER(CView), ctypes.c_int32,
                   ctypes.POINTER(ImageSpec), ctypes.c_uint32, ctypes.c_void_p, ctypes.POINTER(TuneResult)],
                  ctypes.c_int),
@@ -289,6 +291,18 @@ class Context:
                                        _stream_handle(stream))
         _check(self.lib, rc)
         return (out, cnt) if samples else out
+
+    def render_batch_noalloc(self, vol: int, views, out, *, launch=None, stream=None):
+        """``render_batch`` into the caller's device tensor ``out`` [n][H][W]
+        without any allocation by the library (its scratch is a fixed
+        device array; at most 1024 views per call)."""
+        views = list(views)
+        arr = (CView * len(views))(*[_cview(v) for v in views])
+        spec = self._spec(views[0], out.data_ptr(), None)
+        rc = self.lib.gbd_render_batch_noalloc(self.handle, int(vol), arr, len(views), ctypes.byref(spec),
+                                               _launch(launch), _stream_handle(stream))
+        _check(self.lib, rc)
+        return out
 
     def render_batch_host(self, vol: int, views, out_host, *, launch=None, stream=None):
         """Like ``render_batch`` but the images land in ``out_host``, a host
