@@ -45,7 +45,7 @@ RECORD_BYTES = {"f32": 16, "bf16": 8}
 
 
 # ------------------------------------------------------------------ inputs
-def make_workload(name: str, scale: float = 1.0):
+def make_workload(name: str, scale: float = 1.0, device: str = "cpu"):
     import gen
     if name == "time_delay":
         n, size = int(round(256 * scale)), int(round(512 * scale))
@@ -55,12 +55,12 @@ def make_workload(name: str, scale: float = 1.0):
                 "step (theta in {10,45} deg x 9 observer times), retarded-time epoch lerp on")
         return dict(grid=grid, j=j, beta=beta, views=views, store="f32", desc=desc, lookback=True)
     if name == "precision":
-        grid, j, beta, views = gen.config_precision()
+        grid, j, beta, views = gen.config_precision_device(device=device)
         desc = ("precision: 512^3 grid x 8 epochs turbulent jet, stored bf16 j' + fp16 u=Gamma*beta, FP32 "
                 "accumulation; one 1024x1024 view at theta=30, phi=20, t_obs mid-window")
         return dict(grid=grid, j=j, beta=beta, views=views, store="bf16", desc=desc, lookback=True)
     if name == "batched":
-        grid, j, beta, views = gen.config_batched()
+        grid, j, beta, views = gen.config_batched_device(device=device)
         desc = ("batched views: 384^3 grid x 32 epochs FP32 turbulent jet, 256 orientations on a Fibonacci "
                 "sphere, 256x256 each, one persistent graph-captured launch")
         return dict(grid=grid, j=j, beta=beta, views=views, store="f32", desc=desc, lookback=True)
@@ -172,7 +172,7 @@ def run_gpu(args, rank: int, world: int):
 
     dev = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(dev)
-    wl = make_workload(args.workload, args.scale)
+    wl = make_workload(args.workload, args.scale, device=f"cuda:{dev}")
     views = wl["views"]
     n_views = len(views)
     ctx = Context(dev)
@@ -181,8 +181,19 @@ def run_gpu(args, rank: int, world: int):
     torch.cuda.synchronize()
     t_load = time.perf_counter() - t_load
     info = ctx.volume_info(vol)
+    if isinstance(wl["j"], torch.Tensor) and wl["j"].is_cuda:
+        # the packed volume is resident; keep host copies of the inputs only
+        # for the CPU oracle baseline
+        wl["j"] = wl["j"].cpu().numpy()
+        wl["beta"] = wl["beta"].cpu().numpy()
+        torch.cuda.empty_cache()
     stream = torch.cuda.Stream()
     launch = None
+    tuned = None
+    if not args.no_tune:
+        # autotune the launch (and, with --tune-layout, the volume layout) before timing
+        tuned = ctx.tune(vol, views, launch=True, layout=args.tune_layout, stream=stream)
+        info = ctx.volume_info(vol)
 
     # cell-samples of one step (counted once, outside the timed region)
     with torch.cuda.stream(stream):
@@ -257,7 +268,9 @@ def run_gpu(args, rank: int, world: int):
                    "cell_samples_per_step": samples_per_step,
                    "volume_bytes": info["bytes"], "l2": "inputs larger than L2 (resident volume %.1f GB)"
                    % (info["bytes"] / 1e9), "parallelism": "replicas" if world > 1 else "single GPU",
-                   "layout": f"brick {info['brick']}, super-brick {info['super_brick']}"},
+                   "layout": f"brick {info['brick']}, super-brick {info['super_brick']}",
+                   "launch": ({k: tuned[k] for k in ("packet", "cta_warps", "depth", "persistent", "regcap")}
+                              if tuned else "default")},
         "images_per_s": round(world * n_views / (ms_per_step * 1e-3), 2),
         "rays_per_s": round(world * n_views * views[0].width * views[0].height / (ms_per_step * 1e-3), 1),
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
@@ -300,7 +313,10 @@ def oracle_sample(wl, seconds: float, seed: int = 0):
 
 
 def run_reference(args, rank: int):
-    wl = make_workload(args.workload, args.scale)
+    wl = make_workload(args.workload, args.scale, device="cpu")
+    for key in ("j", "beta"):
+        if hasattr(wl[key], "numpy"):
+            wl[key] = wl[key].numpy()
     per_step = []
     n_pix = 0
     threads = 1
@@ -334,6 +350,8 @@ def main():
                          "smaller cases are for profiling)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="oracle work for the cpu_baseline key")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-tune", action="store_true", help="skip the launch autotuner (default configuration)")
+    ap.add_argument("--tune-layout", action="store_true", help="also autotune the volume's brick layout")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")

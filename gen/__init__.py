@@ -28,7 +28,8 @@ __all__ = [
     "Grid", "View", "view_from_angles", "fibonacci_directions", "splitmix64",
     "uniform01", "normal", "conical_jet", "gaussian_blob", "uniform_fields",
     "config_tiny", "config_time_delay", "twin_ejecta", "kolmogorov",
-    "config_precision", "config_batched", "view_from_direction",
+    "config_precision", "config_batched", "view_from_direction", "kolmogorov_torch",
+    "turbulent_jet_torch", "config_precision_device", "config_batched_device",
 ]
 
 
@@ -286,7 +287,7 @@ def kolmogorov(shape, seed: int, stream: int = 0, *, slope: float = -11.0 / 3.0,
         kk = np.where(np.isfinite(k), k, 0.0).astype(np.float32)
         phase = phase + np.float32(t) * (kk * np.float32(max(nx, ny, nz))) ** np.float32(2.0 / 3.0)
     spec = (amp * np.exp(1j * phase)).astype(np.complex64)
-    field = np.fft.irfftn(spec, s=(nz, ny, nx)).astype(np.float64)
+    field = np.fft.irfftn(spec, s=(nz, ny, nx), axes=(0, 1, 2)).astype(np.float64)
     field -= field.mean()
     rms = field.std()
     return field / rms if rms > 0 else field
@@ -348,4 +349,86 @@ def config_batched(seed: int = 4, n: int = 384, n_epochs: int = 32, size: int = 
     t_mid = 0.5 * (n_epochs - 1) * c_dt
     views = [view_from_direction(grid, -d, size=size, c=1.0, t_obs=t_mid)
              for d in fibonacci_directions(n_views)]
+    return grid, j, beta, views
+
+
+# --------------------------------------------------------------------------
+# Device-side builders for the full-size turbulent configurations
+# --------------------------------------------------------------------------
+def kolmogorov_torch(shape, seed: int, stream: int, *, t: float = 0.0, device="cuda", slope: float = -11.0 / 3.0):
+    """Same recipe as ``kolmogorov`` (random Fourier phases, amplitude
+    k^(slope/2), phase advance t (k N)^(2/3), zero mean, unit rms) built with
+    torch on ``device`` from a torch generator seeded with (seed, stream).
+    The numbers differ from the numpy variant; each is reproducible on its
+    own device type."""
+    import torch
+    nz, ny, nx = shape
+    g = torch.Generator(device=device)
+    g.manual_seed((int(seed) * 1000003 + int(stream)) & 0x7FFFFFFFFFFFFFFF)
+    kz = torch.fft.fftfreq(nz, device=device)[:, None, None]
+    ky = torch.fft.fftfreq(ny, device=device)[None, :, None]
+    kx = torch.fft.rfftfreq(nx, device=device)[None, None, :]
+    k = torch.sqrt(kx * kx + ky * ky + kz * kz)
+    amp = torch.where(k > 0, k.clamp_min(1e-12) ** (slope / 2.0), torch.zeros_like(k))
+    phase = torch.rand(k.shape, generator=g, device=device) * (2.0 * math.pi)
+    if t != 0.0:
+        phase = phase + t * (k * max(nx, ny, nz)) ** (2.0 / 3.0)
+    spec = torch.polar(amp, phase)
+    del amp, phase, k
+    field = torch.fft.irfftn(spec, s=(nz, ny, nx))
+    del spec
+    field -= field.mean()
+    rms = field.std()
+    return field / rms if float(rms) > 0 else field
+
+
+def turbulent_jet_torch(grid: Grid, seed: int, device="cuda"):
+    """The turbulent jet of ``config_precision`` built on ``device``:
+    returns float32 tensors j[M][nz][ny][nx] and beta[M][nz][ny][nx][3]."""
+    import torch
+    nx, ny, nz = grid.n
+    M = grid.n_epochs
+    shape = (nz, ny, nx)
+    apex = (float(grid.center[0]), float(grid.center[1]), float(grid.origin[2] + grid.extent[2] / 16.0))
+    x = torch.tensor(grid.cell_centres(0), dtype=torch.float32, device=device)[None, None, :]
+    y = torch.tensor(grid.cell_centres(1), dtype=torch.float32, device=device)[None, :, None]
+    z = torch.tensor(grid.cell_centres(2), dtype=torch.float32, device=device)[:, None, None]
+    r = z - apex[2]
+    rr = r.clamp_min(1.0)
+    sig = rr * math.tan(math.radians(5.0))
+    rho2 = (x - apex[0]) ** 2 + (y - apex[1]) ** 2
+    core = torch.exp(-rho2 / (2.0 * sig * sig))
+    base = torch.where(r >= 0, rr ** -2.0 * core, torch.zeros_like(core))
+    j = torch.empty((M, nz, ny, nx), dtype=torch.float32, device=device)
+    beta = torch.empty((M, nz, ny, nx, 3), dtype=torch.float32, device=device)
+    for m in range(M):
+        tt = 0.05 * m
+        j[m] = base * torch.exp(0.3 * kolmogorov_torch(shape, seed, 0, t=tt, device=device)) + 1e-3
+        mag = (0.5 + 0.49 * core + 0.05 * kolmogorov_torch(shape, seed, 1, t=tt, device=device)).clamp(0.5, 0.99)
+        dxv = torch.sin(0.1 * kolmogorov_torch(shape, seed, 2, t=tt, device=device))
+        dyv = torch.sin(0.1 * kolmogorov_torch(shape, seed, 3, t=tt, device=device))
+        dzv = torch.sqrt((1.0 - dxv * dxv - dyv * dyv).clamp_min(0.0))
+        beta[m, ..., 0] = mag * dxv
+        beta[m, ..., 1] = mag * dyv
+        beta[m, ..., 2] = mag * dzv
+    return j, beta
+
+
+def config_precision_device(seed: int = 3, n: int = 512, n_epochs: int = 8, size: int = 1024, device="cuda"):
+    """``config_precision`` at full size with the fields built on ``device``."""
+    c_dt = n / 4.0
+    grid = Grid(n=(n, n, n), n_epochs=n_epochs, t0=0.0, dt=c_dt)
+    j, beta = turbulent_jet_torch(grid, seed, device)
+    view = view_from_angles(grid, 30.0, 20.0, size=size, c=1.0)
+    return grid, j, beta, [view.with_(t_obs=0.5 * (n_epochs - 1) * c_dt)]
+
+
+def config_batched_device(seed: int = 4, n: int = 384, n_epochs: int = 32, size: int = 256, n_views: int = 256,
+                          device="cuda"):
+    """``config_batched`` at full size with the fields built on ``device``."""
+    c_dt = n / 16.0
+    grid = Grid(n=(n, n, n), n_epochs=n_epochs, t0=0.0, dt=c_dt)
+    j, beta = turbulent_jet_torch(grid, seed, device)
+    t_mid = 0.5 * (n_epochs - 1) * c_dt
+    views = [view_from_direction(grid, -d, size=size, c=1.0, t_obs=t_mid) for d in fibonacci_directions(n_views)]
     return grid, j, beta, views

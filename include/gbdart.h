@@ -154,6 +154,7 @@ typedef struct {
     int32_t cta_warps;           /* warps per CTA: 1, 2, 4 or 8                     */
     int32_t depth;               /* cells gathered ahead per lane: 1, 2 or 4       */
     int32_t persistent;          /* 1 = persistent grid over a tile queue           */
+    int32_t regcap;              /* 1 = kernel built for at most 80 registers/thread */
 } gbd_launch;
 
 /* Description of a resident volume. */
@@ -235,6 +236,74 @@ int gbd_render_batch_noalloc(gbd_ctx *ctx, gbd_volume vol, const gbd_view *views
 /* Number of kernels the last successful render call of this thread
  * launched (graph replays count their kernels). */
 int32_t gbd_last_launch_count(void);
+
+/* ------------------------------------------------------------ serving
+ * Continuous batching of render requests against resident volumes.  Requests
+ * of any volume, storage, image size and orientation are queued; a scheduler
+ * thread of the context admits them into waves as request slots and device
+ * memory free up (a request holds its library-side device bytes -- its image,
+ * when the output is host memory -- from launch to completion) and runs each
+ * wave as one persistent launch over all of its requests' pixel tiles.  Up to
+ * max_waves waves are on the GPU at once on separate streams, so requests that
+ * arrive while others run start as soon as the GPU has room.  Every pixel is
+ * computed by the same per-ray code as gbd_render, so a request's image is the
+ * same whether it is served alone or in a mix.  A volume with queued or
+ * running requests cannot be unloaded or re-laid-out (GBD_ERR_BUSY).  Do not
+ * call gbd_serve_stop or gbd_destroy while other threads poll or wait. */
+typedef struct {
+    gbd_volume volume;
+    gbd_view view;
+    gbd_image_spec spec;     /* out: device memory, or pinned host memory with
+                                out_on_host (pageable host memory is rejected) */
+    int32_t priority;        /* higher first; arrival order within a priority */
+} gbd_request;
+
+typedef struct {
+    int32_t status;          /* final status of the request                  */
+    double queue_ms;         /* submission to the launch of its wave         */
+    double latency_ms;       /* submission to the end of its wave on the GPU */
+    double device_ms;        /* GPU time of its wave                         */
+} gbd_stats;
+
+typedef struct {
+    int32_t max_waves;               /* waves on the GPU at once (default 3, at most 8)  */
+    int32_t max_requests_per_wave;   /* default 256, at most 4096                       */
+    int32_t max_requests_in_flight;  /* request slots (default 1024)                    */
+    uint64_t request_budget_bytes;   /* device bytes for running requests; 0 = what the
+                                        volumes leave of the context budget              */
+    gbd_launch launch;               /* wave kernel configuration (depth 1 or 2)         */
+} gbd_serve_config;
+
+typedef struct {
+    uint64_t completed;              /* requests finished since the last reset    */
+    double p50_ms, p99_ms, max_ms;   /* submission-to-done latency percentiles    */
+    double requests_per_s;           /* completed / (last done - first submission) */
+    uint64_t waves;                  /* waves launched                            */
+    double mean_requests_per_wave;
+    int32_t max_waves_in_flight;     /* most waves seen on the GPU at once        */
+    int32_t pending, in_flight;      /* requests queued / running now             */
+} gbd_serve_summary;
+
+/* Starts the scheduler (config may be NULL for defaults).  gbd_submit starts
+ * it with defaults if needed. */
+int gbd_serve_start(gbd_ctx *ctx, const gbd_serve_config *config);
+/* Cancels queued requests, lets running waves finish, stops the scheduler. */
+int gbd_serve_stop(gbd_ctx *ctx);
+/* Queues a request; *ticket identifies it.  GBD_ERR_BUDGET if it can never
+ * fit the serving budget; GBD_ERR_NOTFOUND for an unknown volume. */
+int gbd_submit(gbd_ctx *ctx, const gbd_request *req, uint64_t *ticket);
+/* Non-blocking: *done = 1 once the request has ended (its stats then hold the
+ * final status, which is also returned); a finished request is reported once. */
+int gbd_poll(gbd_ctx *ctx, uint64_t ticket, int32_t *done, gbd_stats *stats);
+/* Waits up to timeout_ms for the request; GBD_ERR_TIMEOUT if it is still
+ * queued or running (it stays valid and can be waited for again). */
+int gbd_wait(gbd_ctx *ctx, uint64_t ticket, uint32_t timeout_ms, gbd_stats *stats);
+/* A queued request is removed; a running one drains and ends with
+ * GBD_ERR_CANCELLED (its output may have been written). */
+int gbd_cancel(gbd_ctx *ctx, uint64_t ticket);
+/* Latency percentiles and throughput of completed requests; reset != 0
+ * clears the counters after reading. */
+int gbd_serve_stats(gbd_ctx *ctx, int32_t reset, gbd_serve_summary *out);
 
 /* ------------------------------------------------------------ autotuning
  * The paper runs one kernel shape; the launch configuration (warp packet

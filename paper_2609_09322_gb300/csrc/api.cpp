@@ -136,50 +136,68 @@ int make_view(const Volume &vol, const gbd_view &v, int width, int height, doubl
     const double hu = fov_u / width, hv = fov_v / height;
     const double a0 = (0.5 - 0.5 * width) * hu, b0 = (0.5 - 0.5 * height) * hv;
     std::memset(&out, 0, sizeof(out));
+    const gbd_grid &g = vol.grid;
+    const int M = g.n_epochs;
+    const double t0 = g.t0, dt = g.dt;
+    const double two40 = 1099511627776.0, two32 = 4294967296.0;
+    // Epoch coordinate u(s) = u_obs - kk s (Eq. 2 with t_m = t0 + m dt).
+    const bool lookback = (v.flags & GBD_LOOKBACK) != 0u;
+    double u_obs = (v.t_obs - t0) / dt;
+    double kk = 0.0;
+    double win_lo = -HUGE_VAL, win_hi = HUGE_VAL;
+    if (lookback) {
+        if (std::isinf(v.c)) {
+            if (!(u_obs > -1.0 && u_obs < static_cast<double>(M))) win_lo = HUGE_VAL, win_hi = -HUGE_VAL;
+        } else {
+            // Retarded times inside (t0 - dt, t0 + M dt) reach a stored snapshot
+            // (Eq. 9 over the stored m): s = c (t_obs - t_bar).
+            kk = 1.0 / (v.c * dt);
+            win_lo = v.c * (v.t_obs - t0 - M * dt);
+            win_hi = v.c * (v.t_obs - t0 + dt);
+        }
+    } else {
+        u_obs = std::min(std::max(u_obs, 0.0), static_cast<double>(M - 1));
+    }
+    double max_a = 0.0, reach = 0.0;
     for (int i = 0; i < 3; ++i) {
-        out.r00[i] = v.center[i] + a0 * eu[i] + b0 * ev[i];
-        out.du[i] = hu * eu[i];
-        out.dv[i] = hv * ev[i];
-        out.sh[i] = sh[i];
-        out.inv_sh[i] = sh[i] != 0.0 ? 1.0 / sh[i] : 0.0;
-        out.inv_sh_f[i] = sh[i] != 0.0 ? static_cast<float>(1.0 / sh[i]) : 0.0f;
+        const double r00 = v.center[i] + a0 * eu[i] + b0 * ev[i];
+        const double g00 = (r00 - g.origin[i]) / g.dx[i];
+        const double gu = hu * eu[i] / g.dx[i], gv = hv * ev[i] / g.dx[i];
+        // every pixel position must stay within the fixed-point range
+        reach = std::max(reach, std::fabs(g00) + std::fabs(gu) * width + std::fabs(gv) * height + g.n[i]);
+        out.g0[i] = std::llround(g00 * two40);
+        out.gu[i] = std::llround(gu * two40);
+        out.gv[i] = std::llround(gv * two40);
+        // Components below 1e-9 count as parallel: such a ray moves less than
+        // 1e-9 cells per unit length along that axis.
+        const double a = std::fabs(sh[i]) < 1e-9 ? 0.0 : sh[i] / g.dx[i];
+        out.a_hi[i] = static_cast<float>(a);
+        out.a_lo[i] = static_cast<float>(a - static_cast<double>(out.a_hi[i]));
+        out.inv_a[i] = a != 0.0 ? static_cast<float>(1.0 / a) : 0.0f;
+        const double w = a != 0.0 ? kk / a : 0.0;
+        out.w_hi[i] = static_cast<float>(w);
+        out.w_lo[i] = static_cast<float>(w - static_cast<double>(out.w_hi[i]));
+        out.du[i] = std::llround(std::fabs(w) * two32);
+        max_a = std::max(max_a, std::fabs(a));
         out.sh_hi[i] = static_cast<float>(sh[i]);
         out.sh_lo[i] = static_cast<float>(sh[i] - static_cast<double>(out.sh_hi[i]));
     }
-    const int M = vol.grid.n_epochs;
-    const double t0 = vol.grid.t0, dt = vol.grid.dt;
-    out.t_obs = v.t_obs;
+    if (!(max_a > 0.0)) return fail(GBD_ERR_INVALID, "view: direction too small");
+    if (reach > 4.0e6)
+        return fail(GBD_ERR_INVALID, "view: image or grid farther than 4e6 cells from the grid origin");
+    // The epoch coordinate along any ray stays within |u_obs| + kk * (path length).
+    const double path = reach * std::sqrt(3.0) * std::max(g.dx[0], std::max(g.dx[1], g.dx[2]));
+    if (std::fabs(u_obs) + kk * path > 1.0e8)
+        return fail(GBD_ERR_INVALID, "view: observer time or c*dt puts the rays more than 1e8 snapshots away");
+    out.u_obs = std::llround(u_obs * two32);
+    out.kk_hi = static_cast<float>(kk);
+    out.kk_lo = static_cast<float>(kk - static_cast<double>(out.kk_hi));
+    const float fbig = 3.0e38f;
+    out.win_lo = win_lo <= -1e38 ? -fbig : (win_lo >= 1e38 ? fbig : static_cast<float>(win_lo - 1e-6 * (1.0 + std::fabs(win_lo))));
+    out.win_hi = win_hi >= 1e38 ? fbig : (win_hi <= -1e38 ? -fbig : static_cast<float>(win_hi + 1e-6 * (1.0 + std::fabs(win_hi))));
     out.flags = v.flags;
     out.expo = static_cast<float>(2.0 - v.alpha);
     out.prefactor = static_cast<float>(std::pow(v.nu_ratio, v.alpha));
-    const double inf = HUGE_VAL;
-    if (v.flags & GBD_LOOKBACK) {
-        if (std::isinf(v.c)) {
-            out.inv_c = 0.0;
-            const double u = (v.t_obs - t0) / dt;
-            const bool any = u > -1.0 && u < static_cast<double>(M);
-            out.win_lo = any ? -inf : inf;
-            out.win_hi = any ? inf : -inf;
-        } else {
-            // Retarded times inside (t0 - dt, t0 + M dt) reach a stored
-            // snapshot (Eq. 9 over stored m); s = c (t_obs - t_bar).
-            out.inv_c = 1.0 / v.c;
-            const double lo = v.c * (v.t_obs - t0 - M * dt), hi = v.c * (v.t_obs - t0 + dt);
-            const double slack = 1e-9 * (std::fabs(lo) + std::fabs(hi)) + 1e-9;
-            out.win_lo = lo - slack;
-            out.win_hi = hi + slack;
-        }
-        out.u_fast = 0.0f;
-    } else {
-        out.inv_c = 0.0;
-        out.win_lo = -inf;
-        out.win_hi = inf;
-        double u = (v.t_obs - t0) / dt;
-        u = std::min(std::max(u, 0.0), static_cast<double>(M - 1));
-        out.u_fast = static_cast<float>(u);
-        // the float rounding of u must not leave [0, M-1]
-        if (out.u_fast > static_cast<float>(M - 1)) out.u_fast = static_cast<float>(M - 1);
-    }
     if (!(out.prefactor > 0.0f) || !std::isfinite(out.prefactor))
         return fail(GBD_ERR_INVALID, "view: nu_ratio^alpha is not a positive float");
     return GBD_OK;
@@ -192,28 +210,22 @@ VolDev vol_dev(const Volume &v)
     d.rec = v.rec;
     d.axis_off = v.axis_off;
     d.epoch_stride = v.epoch_stride;
-    for (int i = 0; i < 3; ++i) {
-        d.n[i] = v.grid.n[i];
-        d.origin[i] = v.grid.origin[i];
-        d.dx[i] = v.grid.dx[i];
-        d.inv_dx[i] = 1.0 / v.grid.dx[i];
-    }
+    for (int i = 0; i < 3; ++i) d.n[i] = v.grid.n[i];
     d.M = v.grid.n_epochs;
-    d.t0 = v.grid.t0;
-    d.inv_dt = 1.0 / v.grid.dt;
     d.store = v.store;
     return d;
 }
 
 LaunchCfg resolve_launch(const gbd_launch *l)
 {
-    LaunchCfg c{8, 4, 8, 2, 1};
+    LaunchCfg c{8, 4, 8, 2, 1, 0};
     if (l) {
         if (l->packet_w > 0) c.packet_w = l->packet_w;
         if (l->packet_h > 0) c.packet_h = l->packet_h;
         if (l->cta_warps > 0) c.cta_warps = l->cta_warps;
         if (l->depth > 0) c.depth = l->depth;
         c.persistent = l->persistent != 0;
+        c.regcap = l->regcap != 0;
     }
     return c;
 }
@@ -650,7 +662,7 @@ int gbd_unload(gbd_ctx *ctx, gbd_volume vid)
     std::lock_guard<std::mutex> lock(ctx->mu);
     Volume *v = ctx->find(vid);
     if (!v) return fail(GBD_ERR_NOTFOUND, "unknown volume %llu", static_cast<unsigned long long>(vid));
-    if (v->pinned_by_requests > 0) return fail(GBD_ERR_BUSY, "volume has %d queued requests", v->pinned_by_requests);
+    if (v->pinned_by_requests.load() > 0) return fail(GBD_ERR_BUSY, "volume has %d queued requests", v->pinned_by_requests.load());
     DeviceGuard guard(ctx->device);
     drop_graphs_for(*ctx, vid);
     // Work already enqueued on other streams may still read the volume.

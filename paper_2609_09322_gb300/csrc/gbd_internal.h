@@ -25,33 +25,36 @@ struct VolDev {
     long long epoch_stride;   // records per epoch (padded)
     int n[3];
     int M;
-    double origin[3];
-    double dx[3];
-    double inv_dx[3];
-    double t0, inv_dt;
     int store;                // GBD_STORE_*
 };
 
-// Per-view constants, computed on the host in float64 once per view (camera
-// basis, pixel pitch, lookback window, power-law prefactor).
+// Per-view constants, computed on the host in float64 once per view, so that
+// the kernels need no float64 arithmetic (the FP64 rate of GB300 is 1/64 of
+// FP32).  Lengths along a ray are the parameter s of x = r0 + s s_hat, with s
+// measured from the image plane; positions are in grid-index units
+// g_i = (x_i - origin_i) / dx_i, so cell faces sit at integers.
+//   fixed point: Q24.40 (int64, 2^-40 cells per unit) for positions,
+//                Q31.32 (int64, 2^-32 epochs per unit) for epoch coordinates.
 struct ViewDev {
-    double r00[3];     // centre of pixel (0, 0)
-    double du[3];      // h_u e_u: step between pixel columns
-    double dv[3];      // h_v e_v: step between pixel rows
-    double sh[3];      // s_hat
-    double inv_sh[3];  // 1 / s_hat_i, 0 where s_hat_i = 0
-    double t_obs;
-    double inv_c;      // 1/c, 0 for c = infinity
-    double win_lo;     // lookback window of s where t_bar lies in [t_0, t_{M-1}]
-    double win_hi;
+    long long g0[3];   // pixel (0, 0) on the image plane, Q24.40
+    long long gu[3];   // change per pixel column, Q24.40
+    long long gv[3];   // change per pixel row, Q24.40
+    long long u_obs;   // epoch coordinate at s = 0, Q31.32 (fast light: the clamped one)
+    long long du[3];   // epochs crossed per face plane of axis i, kk / |a_i|, Q31.32
+    float a_hi[3];     // a_i = s_hat_i / dx_i (cells per unit s) as hi + lo floats;
+    float a_lo[3];     //   0 for an axis the ray runs parallel to
+    float inv_a[3];    // 1 / a_i (face spacing along the ray, Eq. 11), 0 if parallel
+    float w_hi[3];     // kk / a_i as hi + lo floats
+    float w_lo[3];
+    float kk_hi;       // kk = 1 / (c dt): epochs per unit s (0 without lookback)
+    float kk_lo;
+    float win_lo;      // s range where the retarded time can reach a snapshot
+    float win_hi;
     float sh_hi[3];    // s_hat rounded to float ...
-    float sh_lo[3];    // ... and the rounding residual
-    float inv_sh_f[3]; // float 1 / s_hat_i (0 where s_hat_i = 0)
-    float u_fast;      // epoch coordinate without lookback, clamped to [0, M-1]
+    float sh_lo[3];    // ... and the rounding residual (Doppler dot product)
     float expo;        // 2 - alpha
     float prefactor;   // (nu / nu'_0)^alpha
     uint32_t flags;    // GBD_BEAMING | GBD_LOOKBACK
-    int32_t pad_;
 };
 
 // One march launch: n_views views of one image geometry.
@@ -70,14 +73,36 @@ struct MarchArgs {
     int persistent;
 };
 
+// One request of a served wave: its own volume, view, image and outputs.
+struct ReqDev {
+    VolDev vol;
+    ViewDev view;
+    int width, height;
+    int tiles_x, tiles_y;
+    long long tile_begin;     // first tile of this request in the wave's queue
+    float *out;               // device image of the request
+    uint32_t *samples;        // optional per-pixel cell-sample counts
+};
+
+// A served wave: many requests in one persistent launch.
+struct WaveArgs {
+    const ReqDev *reqs;       // device array, sorted by tile_begin
+    int n_reqs;
+    int packet_w, packet_h;
+    long long total_items;    // tiles of all requests
+    int *queue;               // tile counter (zeroed before launch)
+    int *error_word;
+};
+
 // Launch configuration after defaults have been applied.
 struct LaunchCfg {
-    int packet_w, packet_h, cta_warps, depth, persistent;
+    int packet_w, packet_h, cta_warps, depth, persistent, regcap;
 };
 
 // Kernel entry points (march.cu, pack.cu).
 cudaError_t launch_march(const MarchArgs &a, const LaunchCfg &cfg, int num_sms, cudaStream_t stream);
 cudaError_t march_occupancy(const LaunchCfg &cfg, int store, int smem_bytes, int *blocks_per_sm);
+cudaError_t launch_wave(const WaveArgs &a, const LaunchCfg &cfg, int num_sms, cudaStream_t stream);
 
 struct PackArgs {
     const void *j;            // one epoch, [nz][ny][nx]

@@ -114,144 +114,132 @@ struct Record<GBD_STORE_BF16_F16U> {
 };
 
 #ifdef GBD_CHECKED
-__device__ __forceinline__ bool check_cell(const MarchArgs &a, int ix, int iy, int iz, int m)
+__device__ __forceinline__ bool check_cell(const VolDev &vol, int *err_word, int ix, int iy, int iz, int m)
 {
-    const bool ok = ix >= 0 && ix < a.vol.n[0] && iy >= 0 && iy < a.vol.n[1] && iz >= 0 && iz < a.vol.n[2] &&
-                    m >= 0 && m < a.vol.M;
-    if (!ok && a.error_word) atomicCAS(a.error_word, 0, 1);
+    const bool ok = ix >= 0 && ix < vol.n[0] && iy >= 0 && iy < vol.n[1] && iz >= 0 && iz < vol.n[2] &&
+                    m >= 0 && m < vol.M;
+    if (!ok && err_word) atomicCAS(err_word, 0, 1);
     return ok;
 }
 #endif
 
-// Double-float (hi + lo) arithmetic for the epoch coordinate.  The
-// intrinsics are never contracted into fused multiply-adds, which keeps the
-// error-free transformations exact.
-struct DD {
-    float h, l;
-};
+// The epoch coordinate u = (t_bar - t0) / dt is carried in Q31.32 fixed point
+// (int64, 2^-32 epochs per unit): float32 cannot resolve u to better than half
+// an ulp of the snapshot count (about 4e-6 at u ~ 64), which a fast-changing
+// field amplifies beyond a 1e-5 relative pixel tolerance; integer updates are
+// exact and cheap.
+constexpr float kTwo32 = 4294967296.0f;        // 2^32
+constexpr float kTwo40 = 1099511627776.0f;      // 2^40
+constexpr float kInv2p40 = 9.094947017729282e-13f;  // 2^-40
 
-__device__ __forceinline__ DD two_sum(float a, float b)
+// x (a float) times y = y_hi + y_lo (a double-float), as a fixed-point
+// integer of scale `scale`: the product x * y_hi is split exactly into its
+// rounded value and rounding error with a fused multiply-add, and each part
+// is converted separately, so the result carries about 48 bits of y.
+__device__ __forceinline__ long long dd_mul_fix(float x, float y_hi, float y_lo, float scale)
 {
-    const float s = __fadd_rn(a, b);
-    const float bb = __fsub_rn(s, a);
-    const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
-    return {s, e};
+    const float p = __fmul_rn(x, y_hi);
+    const float e = fmaf(x, y_hi, -p);
+    const float r = fmaf(x, y_lo, e);
+    return __float2ll_rn(p * scale) + __float2ll_rn(r * scale);
 }
 
-__device__ __forceinline__ DD renorm(float h, float l)
+__device__ __forceinline__ float fix_to_float(long long v, float inv_scale)
 {
-    const float s = __fadd_rn(h, l);
-    return {s, __fsub_rn(l, __fsub_rn(s, h))};
+    return __ll2float_rn(v) * inv_scale;
 }
 
-// A - B * k for double-float A, B and a small integer k (exact in float).
-__device__ __forceinline__ DD dd_sub_mul(DD A, DD B, float k)
-{
-    const float p = __fmul_rn(B.h, k);
-    const float pe = fmaf(B.h, k, -p);  // B.h * k = p + pe exactly
-    const DD s = two_sum(A.h, -p);
-    const float l = __fadd_rn(s.l, __fsub_rn(__fsub_rn(A.l, pe), __fmul_rn(B.l, k)));
-    return renorm(s.h, l);
-}
-
-__device__ __forceinline__ DD dd_mid(DD a, DD b)
-{
-    const DD s = two_sum(a.h, b.h);
-    const DD r = renorm(s.h, __fadd_rn(s.l, __fadd_rn(a.l, b.l)));
-    return {0.5f * r.h, 0.5f * r.l};
-}
-
-__device__ __forceinline__ DD to_dd(double x)
-{
-    const float h = static_cast<float>(x);
-    return {h, static_cast<float>(x - static_cast<double>(h))};
-}
-
+// Marches the ray of pixel (p, q) of one image and stores its value (and,
+// if cnt_img is set, its cell-sample count).  out_img points at the image.
 template <int STORE, int DEPTH>
-__device__ __forceinline__ void march_ray(const MarchArgs &a, const ViewDev &V, int vi, int p, int q,
+__device__ __forceinline__ void march_ray(const VolDev &vol, const ViewDev &V, int p, int q, int width, int height,
+                                          float *out_img, uint32_t *cnt_img, int *err_word,
                                           const int32_t *__restrict__ offx, const int32_t *__restrict__ offy,
                                           const int32_t *__restrict__ offz)
 {
     using Rec = Record<STORE>;
-    const VolDev &vol = a.vol;
-    const bool in_image = (p < a.width) && (q < a.height);
+    const bool in_image = (p < width) && (q < height);
     bool alive = in_image;
 
-    // ---------------- ray setup, float64, once per ray ----------------
-    double r0[3], lo[3], hi[3];
+    // ---------------- ray setup, once per ray, no float64 ----------------
+    // Pixel position on the image plane in grid-index units (Q24.40, exact
+    // integer arithmetic from the per-view constants).
+    long long g0[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+        g0[i] = V.g0[i] + static_cast<long long>(p) * V.gu[i] + static_cast<long long>(q) * V.gv[i];
+    // Estimated start of the traversal: the later of the box entry and the
+    // window start.  This anchor only has to be a point of the ray no more
+    // than a cell past the true start (crossings are measured from it, so it
+    // should be close to keep them accurate); it may lie outside the box.
+    float s_in_e = -3.0e38f, s_out_e = 3.0e38f;
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-        r0[i] = fma(static_cast<double>(q), V.dv[i], fma(static_cast<double>(p), V.du[i], V.r00[i]));
-        lo[i] = vol.origin[i];
-        hi[i] = fma(static_cast<double>(vol.n[i]), vol.dx[i], vol.origin[i]);
-    }
-    double s_in = -DBL_MAX, s_out = DBL_MAX;
-#pragma unroll
-    for (int i = 0; i < 3; ++i) {
-        if (V.inv_sh[i] != 0.0) {
-            const double t1 = (lo[i] - r0[i]) * V.inv_sh[i];
-            const double t2 = (hi[i] - r0[i]) * V.inv_sh[i];
-            s_in = fmax(s_in, fmin(t1, t2));
-            s_out = fmin(s_out, fmax(t1, t2));
-        } else if (r0[i] < lo[i] || r0[i] >= hi[i]) {
-            alive = false;
+        if (V.inv_a[i] != 0.f) {
+            const float gf = fix_to_float(g0[i], kInv2p40);
+            const float t1 = -gf * V.inv_a[i];
+            const float t2 = (static_cast<float>(vol.n[i]) - gf) * V.inv_a[i];
+            s_in_e = fmaxf(s_in_e, fminf(t1, t2));
+            s_out_e = fminf(s_out_e, fmaxf(t1, t2));
+        } else if (g0[i] < 0 || g0[i] >= (static_cast<long long>(vol.n[i]) << 40)) {
+            alive = false;  // parallel to this axis and outside the box along it
         }
     }
-    // Fast-forward: the traversal starts in the cell holding the first point
-    // whose retarded time can reach a stored snapshot (Sec. 5.1).
-    const double s0 = fmax(s_in, V.win_lo);
-    if (!(fmin(s_out, V.win_hi) > s0)) alive = false;
+    const float s_a = fmaxf(s_in_e, V.win_lo);
+    if (!(fminf(s_out_e, V.win_hi) > s_a - 1e-3f * (1.f + fabsf(s_a)))) alive = false;
+    const float sa = alive ? s_a : 0.f;
 
-    // Epoch coordinate u = (t_bar - t0) / dt = u0 - kk * s_local (Eq. 2).
-    const bool lookback = (V.flags & GBD_LOOKBACK) != 0u;
-    const double u0 = lookback ? (V.t_obs - s0 * V.inv_c - vol.t0) * vol.inv_dt : static_cast<double>(V.u_fast);
-    const double kk = lookback ? V.inv_c * vol.inv_dt : 0.0;
-
-    // Per axis: entry cell index, local origin o (entry point minus the cell's
-    // lower corner), and the epoch coordinate at that axis' face planes,
-    // u(k) = A - B k for the plane k cells above the entry cell's lower face,
-    // evaluated from float64 constants kept as double-floats.
-    int idx[3], step[3], base_idx[3], nk[3];
-    float o[3], dxf[3], inv_d[3];
-    DD A[3], B[3];
+    // Anchor: the point s_a of the ray, in exact fixed point; its cell, the
+    // position o inside that cell, and per axis the face spacing along the
+    // ray (inv_a, Eq. 11), so that the crossing of the plane k cells above the
+    // anchor cell's lower face is at s_a + k inv_a - o inv_a.
+    int idx[3], step[3], nk[3];
+    float of[3];
+    long long un[3];
+    float s_lo_box = -3.0e38f, s_hi_box = 3.0e38f;  // box chord relative to the anchor
+    // epoch coordinate at the anchor: u_obs - kk s_a
+    const long long u_a = V.u_obs - dd_mul_fix(sa, V.kk_hi, V.kk_lo, kTwo32);
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-        const double xe = fma(s0, V.sh[i], r0[i]);
-        int k = __double2int_rd((xe - lo[i]) * vol.inv_dx[i]);
+        const bool moving = V.inv_a[i] != 0.f;
+        const long long ga = moving ? g0[i] + dd_mul_fix(sa, V.a_hi[i], V.a_lo[i], kTwo40) : g0[i];
+        int k = static_cast<int>(ga >> 40);
         k = min(max(k, 0), vol.n[i] - 1);
         idx[i] = k;
-        base_idx[i] = k;
-        const double od = alive ? xe - fma(static_cast<double>(k), vol.dx[i], lo[i]) : 0.0;
-        o[i] = static_cast<float>(od);
-        dxf[i] = static_cast<float>(vol.dx[i]);
-        inv_d[i] = V.inv_sh_f[i];
-        step[i] = V.sh[i] > 0.0 ? 1 : (V.sh[i] < 0.0 ? -1 : 0);
-        nk[i] = step[i] > 0 ? 1 : 0;  // plane of the next crossing
-        A[i] = to_dd(alive ? u0 + kk * od * V.inv_sh[i] : 0.0);
-        B[i] = to_dd(kk * vol.dx[i] * V.inv_sh[i]);
+        const float o = fix_to_float(ga - (static_cast<long long>(k) << 40), kInv2p40);
+        step[i] = V.a_hi[i] > 0.f ? 1 : (V.a_hi[i] < 0.f ? -1 : 0);
+        nk[i] = step[i] > 0 ? 1 : 0;
+        of[i] = o * V.inv_a[i];
+        if (moving) {
+            // box faces (planes 0 and n of this axis) relative to the anchor cell
+            const float t1 = fmaf(static_cast<float>(-k), V.inv_a[i], -of[i]);
+            const float t2 = fmaf(static_cast<float>(vol.n[i] - k), V.inv_a[i], -of[i]);
+            s_lo_box = fmaxf(s_lo_box, fminf(t1, t2));
+            s_hi_box = fminf(s_hi_box, fmaxf(t1, t2));
+        }
+        // u at the next crossing: u_a - kk (nk - o) / a_i
+        un[i] = u_a - dd_mul_fix(static_cast<float>(nk[i]) - o, V.w_hi[i], V.w_lo[i], kTwo32);
     }
-    // Face crossing of plane k of axis i in the local frame (s from s0),
-    // recomputed from the integer index.
-    auto crossing = [&](int i, int k_rel) -> float {
-        return (static_cast<float>(k_rel) * dxf[i] - o[i]) * inv_d[i];
-    };
+    if (!(s_hi_box > s_lo_box)) alive = false;
     float sn[3];
-    float s_cur = -FLT_MAX;
-    DD u_cur = {0.f, 0.f};
+    float s_cur = -3.0e38f;
+    long long u_cur = 0;
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-        sn[i] = step[i] == 0 ? FLT_MAX : crossing(i, nk[i]);
+        sn[i] = step[i] == 0 ? 3.0e38f : fmaf(static_cast<float>(nk[i]), V.inv_a[i], -of[i]);
         if (step[i] != 0) {
-            // the entry cell's own entry face: the latest of its three
-            const int ek = step[i] > 0 ? 0 : 1;
-            const float se = crossing(i, ek);
+            // the anchor cell's own entry face: the latest of its three
+            const float se = fmaf(static_cast<float>(nk[i] - step[i]), V.inv_a[i], -of[i]);
             if (se > s_cur) {
                 s_cur = se;
-                u_cur = dd_sub_mul(A[i], B[i], static_cast<float>(ek));
+                u_cur = un[i] + V.du[i];  // the entry plane is one plane behind the next one
             }
         }
     }
-    const float Mf = static_cast<float>(vol.M);
+    // The march never counts a chord outside the box: a start cell that was
+    // clamped onto the grid yields empty chords until the ray enters.
+    s_cur = fmaxf(s_cur, s_lo_box);
+    const long long u_lo = -(1LL << 32);                          // u = -1
     const int Mm1 = vol.M - 1;
 
     BoostConsts bc;
@@ -260,9 +248,17 @@ __device__ __forceinline__ void march_ray(const MarchArgs &a, const ViewDev &V, 
     bc.expo = V.expo;
     bc.beaming = (V.flags & GBD_BEAMING) != 0u;
 
-    int32_t ox = alive ? offx[idx[0]] : 0;
-    int32_t oy = alive ? offy[idx[1]] : 0;
-    int32_t oz = alive ? offz[idx[2]] : 0;
+    // Table terms of the current cell, and of the next cell along each axis
+    // (prefetched so that a step never waits on shared memory).
+    int32_t ox = 0, oy = 0, oz = 0, px = 0, py = 0, pz = 0;
+    if (alive) {
+        ox = offx[idx[0]];
+        oy = offy[idx[1]];
+        oz = offz[idx[2]];
+        px = offx[min(max(idx[0] + step[0], 0), vol.n[0] - 1)];
+        py = offy[min(max(idx[1] + step[1], 0), vol.n[1] - 1)];
+        pz = offz[min(max(idx[2] + step[2], 0), vol.n[2] - 1)];
+    }
     const long long es = vol.epoch_stride;
     const void *recs = vol.rec;
 
@@ -289,26 +285,21 @@ __device__ __forceinline__ void march_ray(const MarchArgs &a, const ViewDev &V, 
                 // lowest axis (the zero-length chord that follows adds nothing).
                 const bool x0 = sn[0] <= sn[1] && sn[0] <= sn[2];
                 const bool x1 = !x0 && sn[1] <= sn[2];
-                const float s_exit = x0 ? sn[0] : (x1 ? sn[1] : sn[2]);
-                const int kx = x0 ? nk[0] : (x1 ? nk[1] : nk[2]);
-                const DD Ax = x0 ? A[0] : (x1 ? A[1] : A[2]);
-                const DD Bx = x0 ? B[0] : (x1 ? B[1] : B[2]);
-                const DD u_exit = dd_sub_mul(Ax, Bx, static_cast<float>(kx));
+                const float s_exit = fminf(x0 ? sn[0] : (x1 ? sn[1] : sn[2]), s_hi_box);
+                const long long u_exit = x0 ? un[0] : (x1 ? un[1] : un[2]);
                 const float ds = s_exit - s_cur;
                 // epoch coordinate at the chord midpoint: m_bar + w, w in [0, 1)
-                const DD um = dd_mid(u_cur, u_exit);
-                float fm = floorf(um.h);
-                float w = (um.h - fm) + um.l;
-                if (w >= 1.f) { fm += 1.f; w -= 1.f; }
-                if (w < 0.f) { fm -= 1.f; w += 1.f; }
-                const bool inside = (fm > -1.f || (fm == -1.f && w > 0.f)) && fm < Mf;
+                const long long um = (u_cur + u_exit) >> 1;
+                const int mb = static_cast<int>(um >> 32);
+                const uint32_t frac = static_cast<uint32_t>(um);
+                const float w = static_cast<float>(frac) * 2.3283064365386963e-10f;
+                const bool inside = um > u_lo && mb <= Mm1;
                 if (ds > 0.f && inside) {
-                    const int mb = static_cast<int>(fm);
                     has_lo[d] = mb >= 0;
-                    has_hi[d] = (mb < Mm1) && (w > 0.f);
+                    has_hi[d] = (mb < Mm1) && (frac != 0u);
 #ifdef GBD_CHECKED
-                    if ((has_lo[d] && !check_cell(a, idx[0], idx[1], idx[2], mb)) ||
-                        (has_hi[d] && !check_cell(a, idx[0], idx[1], idx[2], mb + 1))) {
+                    if ((has_lo[d] && !check_cell(vol, err_word, idx[0], idx[1], idx[2], mb)) ||
+                        (has_hi[d] && !check_cell(vol, err_word, idx[0], idx[1], idx[2], mb + 1))) {
                         has_lo[d] = has_hi[d] = false;
                     }
 #endif
@@ -318,7 +309,7 @@ __device__ __forceinline__ void march_ray(const MarchArgs &a, const ViewDev &V, 
                 }
                 // Past the last time that reaches a snapshot: nothing further
                 // along the ray can contribute.
-                if (u_exit.h + u_exit.l <= -1.00001f || --steps_left <= 0) {
+                if (u_exit <= u_lo || s_exit >= s_hi_box || --steps_left <= 0) {
                     alive = false;
                 } else if (x0) {
                     const int k = idx[0] + step[0];
@@ -327,8 +318,10 @@ __device__ __forceinline__ void march_ray(const MarchArgs &a, const ViewDev &V, 
                     } else {
                         idx[0] = k;
                         nk[0] += step[0];
-                        sn[0] = crossing(0, nk[0]);
-                        ox = offx[k];
+                        sn[0] = fmaf(static_cast<float>(nk[0]), V.inv_a[0], -of[0]);
+                        un[0] -= V.du[0];
+                        ox = px;
+                        px = offx[min(max(k + step[0], 0), vol.n[0] - 1)];
                     }
                 } else if (x1) {
                     const int k = idx[1] + step[1];
@@ -337,8 +330,10 @@ __device__ __forceinline__ void march_ray(const MarchArgs &a, const ViewDev &V, 
                     } else {
                         idx[1] = k;
                         nk[1] += step[1];
-                        sn[1] = crossing(1, nk[1]);
-                        oy = offy[k];
+                        sn[1] = fmaf(static_cast<float>(nk[1]), V.inv_a[1], -of[1]);
+                        un[1] -= V.du[1];
+                        oy = py;
+                        py = offy[min(max(k + step[1], 0), vol.n[1] - 1)];
                     }
                 } else {
                     const int k = idx[2] + step[2];
@@ -347,12 +342,19 @@ __device__ __forceinline__ void march_ray(const MarchArgs &a, const ViewDev &V, 
                     } else {
                         idx[2] = k;
                         nk[2] += step[2];
-                        sn[2] = crossing(2, nk[2]);
-                        oz = offz[k];
+                        sn[2] = fmaf(static_cast<float>(nk[2]), V.inv_a[2], -of[2]);
+                        un[2] -= V.du[2];
+                        oz = pz;
+                        pz = offz[min(max(k + step[2], 0), vol.n[2] - 1)];
                     }
                 }
-                s_cur = s_exit;
-                u_cur = u_exit;
+                // the next chord starts where this one ended (an empty chord
+                // before the ray enters the box leaves the start unchanged,
+                // with the epoch coordinate that belongs to it)
+                if (s_exit > s_cur) {
+                    s_cur = s_exit;
+                    u_cur = u_exit;
+                }
             }
         }
         typename Rec::T rlo[DEPTH], rhi[DEPTH];
@@ -377,14 +379,16 @@ __device__ __forceinline__ void march_ray(const MarchArgs &a, const ViewDev &V, 
     }
 
     if (in_image) {
-        const long long pix = static_cast<long long>(vi) * a.width * a.height + static_cast<long long>(q) * a.width + p;
-        a.out[pix] = V.prefactor * acc;
-        if (a.samples) a.samples[pix] = count;
+        const long long pix = static_cast<long long>(q) * width + p;
+        out_img[pix] = V.prefactor * acc;
+        if (cnt_img) cnt_img[pix] = count;
     }
 }
 
-template <int STORE, int DEPTH>
-__global__ void __launch_bounds__(256) march_kernel(const MarchArgs a)
+// MINB = 1 leaves the register count to the compiler; MINB = 3 asks for
+// three 256-thread CTAs per SM (at most 80 registers per thread).
+template <int STORE, int DEPTH, int MINB>
+__global__ void __launch_bounds__(256, MINB) march_kernel(const MarchArgs a)
 {
     extern __shared__ int32_t s_off[];
     const int nx = a.vol.n[0], ny = a.vol.n[1], nz = a.vol.n[2];
@@ -413,50 +417,113 @@ __global__ void __launch_bounds__(256) march_kernel(const MarchArgs a)
         const int ty = tile / a.tiles_x;
         const int p = tx * a.packet_w + lane % a.packet_w;
         const int q = ty * a.packet_h + lane / a.packet_w;
-        march_ray<STORE, DEPTH>(a, a.views[vi], vi, p, q, offx, offy, offz);
+        const long long img = static_cast<long long>(vi) * a.width * a.height;
+        march_ray<STORE, DEPTH>(a.vol, a.views[vi], p, q, a.width, a.height, a.out + img,
+                                a.samples ? a.samples + img : nullptr, a.error_word, offx, offy, offz);
         if (!a.persistent) break;
     }
 }
 
-template <int STORE, int DEPTH>
-void *kernel_ptr()
+// Serving: one persistent launch over the tiles of many requests, each with
+// its own volume (float32 or bfloat16/float16 records), view and image.  The
+// layout tables are read from global memory (they differ per request); every
+// ray runs the same march_ray as the single-volume kernel, so a request's
+// pixels are the same whether it is served alone or in a mix.
+template <int DEPTH, int MINB>
+__global__ void __launch_bounds__(256, MINB) wave_kernel(const WaveArgs a)
 {
-    return reinterpret_cast<void *>(&march_kernel<STORE, DEPTH>);
+    const int lane = threadIdx.x & 31;
+    for (;;) {
+        int it = 0;
+        if (lane == 0) it = atomicAdd(a.queue, 1);
+        const long long item = __shfl_sync(kFull, it, 0);
+        if (item >= a.total_items) break;
+        int lo = 0, hi = a.n_reqs - 1;  // last request whose first tile is <= item
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (a.reqs[mid].tile_begin <= item) lo = mid;
+            else hi = mid - 1;
+        }
+        const ReqDev &R = a.reqs[lo];
+        const int tile = static_cast<int>(item - R.tile_begin);
+        const int tx = tile % R.tiles_x;
+        const int ty = tile / R.tiles_x;
+        const int p = tx * a.packet_w + lane % a.packet_w;
+        const int q = ty * a.packet_h + lane / a.packet_w;
+        const int32_t *tab = R.vol.axis_off;
+        const int32_t *ty_tab = tab + R.vol.n[0];
+        const int32_t *tz_tab = ty_tab + R.vol.n[1];
+        if (R.vol.store == GBD_STORE_F32)
+            march_ray<GBD_STORE_F32, DEPTH>(R.vol, R.view, p, q, R.width, R.height, R.out, R.samples, a.error_word,
+                                            tab, ty_tab, tz_tab);
+        else
+            march_ray<GBD_STORE_BF16_F16U, DEPTH>(R.vol, R.view, p, q, R.width, R.height, R.out, R.samples,
+                                                  a.error_word, tab, ty_tab, tz_tab);
+    }
 }
 
-void *select_kernel(int store, int depth)
+template <int STORE, int DEPTH, int MINB>
+void *kernel_ptr()
 {
-    if (store == GBD_STORE_F32) {
-        switch (depth) {
-        case 1: return kernel_ptr<GBD_STORE_F32, 1>();
-        case 2: return kernel_ptr<GBD_STORE_F32, 2>();
-        case 4: return kernel_ptr<GBD_STORE_F32, 4>();
-        default: return nullptr;
-        }
+    return reinterpret_cast<void *>(&march_kernel<STORE, DEPTH, MINB>);
+}
+
+template <int STORE, int MINB>
+void *select_depth(int depth)
+{
+    switch (depth) {
+    case 1: return kernel_ptr<STORE, 1, MINB>();
+    case 2: return kernel_ptr<STORE, 2, MINB>();
+    case 4: return kernel_ptr<STORE, 4, MINB>();
+    default: return nullptr;
     }
-    if (store == GBD_STORE_BF16_F16U) {
-        switch (depth) {
-        case 1: return kernel_ptr<GBD_STORE_BF16_F16U, 1>();
-        case 2: return kernel_ptr<GBD_STORE_BF16_F16U, 2>();
-        case 4: return kernel_ptr<GBD_STORE_BF16_F16U, 4>();
-        default: return nullptr;
-        }
-    }
+}
+
+void *select_kernel(int store, int depth, int capped)
+{
+    if (store == GBD_STORE_F32) return capped ? select_depth<GBD_STORE_F32, 3>(depth) : select_depth<GBD_STORE_F32, 1>(depth);
+    if (store == GBD_STORE_BF16_F16U)
+        return capped ? select_depth<GBD_STORE_BF16_F16U, 3>(depth) : select_depth<GBD_STORE_BF16_F16U, 1>(depth);
+    return nullptr;
+}
+
+void *select_wave(int depth, int capped)
+{
+    if (depth == 1) return capped ? reinterpret_cast<void *>(&wave_kernel<1, 3>) : reinterpret_cast<void *>(&wave_kernel<1, 1>);
+    if (depth == 2) return capped ? reinterpret_cast<void *>(&wave_kernel<2, 3>) : reinterpret_cast<void *>(&wave_kernel<2, 1>);
     return nullptr;
 }
 
 }  // namespace
 
+cudaError_t launch_wave(const WaveArgs &a, const LaunchCfg &cfg, int num_sms, cudaStream_t stream)
+{
+    void *k = select_wave(cfg.depth, cfg.regcap);
+    if (!k) return cudaErrorInvalidValue;
+    const int threads = 32 * cfg.cta_warps;
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, threads, 0);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+    long long blocks = static_cast<long long>(per_sm) * num_sms;
+    const long long needed = (a.total_items + cfg.cta_warps - 1) / cfg.cta_warps;
+    if (blocks > needed) blocks = needed;
+    if (blocks < 1) return cudaSuccess;
+    WaveArgs args = a;
+    void *params[] = {&args};
+    return cudaLaunchKernel(k, dim3(static_cast<unsigned>(blocks)), dim3(threads), params, 0, stream);
+}
+
 cudaError_t march_occupancy(const LaunchCfg &cfg, int store, int smem_bytes, int *blocks_per_sm)
 {
-    void *k = select_kernel(store, cfg.depth);
+    void *k = select_kernel(store, cfg.depth, cfg.regcap);
     if (!k) return cudaErrorInvalidValue;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k, 32 * cfg.cta_warps, smem_bytes);
 }
 
 cudaError_t launch_march(const MarchArgs &a, const LaunchCfg &cfg, int num_sms, cudaStream_t stream)
 {
-    void *k = select_kernel(a.vol.store, cfg.depth);
+    void *k = select_kernel(a.vol.store, cfg.depth, cfg.regcap);
     if (!k) return cudaErrorInvalidValue;
     const int threads = 32 * cfg.cta_warps;
     const int smem = static_cast<int>(sizeof(int32_t)) * (a.vol.n[0] + a.vol.n[1] + a.vol.n[2]);

@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstdint>
 #include <cstring>
 #include <map>
@@ -23,7 +24,7 @@ struct Volume {
     int32_t *axis_off = nullptr;     // per-axis offset tables (n_x + n_y + n_z)
     long long epoch_stride = 0;      // records per epoch
     uint64_t bytes = 0;              // device bytes charged to the budget
-    int pinned_by_requests = 0;      // queued serving requests using it
+    std::atomic<int> pinned_by_requests{0};  // queued or running serving requests using it
 };
 
 struct GraphCache;
@@ -37,7 +38,7 @@ struct TuneKey {
 };
 
 struct TuneEntry {
-    LaunchCfg cfg{8, 4, 8, 2, 1};
+    LaunchCfg cfg{8, 4, 8, 2, 1, 0};
     int brick = 8, super_brick = 4;
     float ms = 0.f;
 };
@@ -109,6 +110,7 @@ void load_tune_file(Ctx &ctx);
 int relayout_volume(Ctx &ctx, Volume &vol, gbd_volume vid, int B, int S);
 
 // Serving (serve.cpp).
+int serve_start(Ctx &ctx, const gbd_serve_config *c);
 void serve_shutdown(Ctx &ctx);
 
 }  // namespace gbd

@@ -55,8 +55,8 @@ void append_cache_file(const TuneKey &k, const TuneEntry &e)
     std::lock_guard<std::mutex> lock(g_file_mu);
     FILE *f = std::fopen(path, "a");
     if (!f) return;
-    std::fprintf(f, "%s -> %d %d %d %d %d %d %d %.6f\n", key_text(k).c_str(), e.cfg.packet_w, e.cfg.packet_h,
-                 e.cfg.cta_warps, e.cfg.depth, e.cfg.persistent, e.brick, e.super_brick, e.ms);
+    std::fprintf(f, "%s -> %d %d %d %d %d %d %d %d %.6f\n", key_text(k).c_str(), e.cfg.packet_w, e.cfg.packet_h,
+                 e.cfg.cta_warps, e.cfg.depth, e.cfg.persistent, e.cfg.regcap, e.brick, e.super_brick, e.ms);
     std::fclose(f);
 }
 
@@ -179,10 +179,10 @@ void load_tune_file(Ctx &ctx)
         TuneKey k;
         std::memset(&k, 0, sizeof(k));
         TuneEntry e;
-        if (std::sscanf(line, "%d %d %d %d %d %d %d %d %d -> %d %d %d %d %d %d %d %f", &k.n[0], &k.n[1], &k.n[2],
-                        &k.M, &k.store, &k.width, &k.height, &k.n_views, &k.lookback, &e.cfg.packet_w,
-                        &e.cfg.packet_h, &e.cfg.cta_warps, &e.cfg.depth, &e.cfg.persistent, &e.brick,
-                        &e.super_brick, &e.ms) == 17 &&
+        if (std::sscanf(line, "%d %d %d %d %d %d %d %d %d -> %d %d %d %d %d %d %d %d %f", &k.n[0], &k.n[1],
+                        &k.n[2], &k.M, &k.store, &k.width, &k.height, &k.n_views, &k.lookback, &e.cfg.packet_w,
+                        &e.cfg.packet_h, &e.cfg.cta_warps, &e.cfg.depth, &e.cfg.persistent, &e.cfg.regcap,
+                        &e.brick, &e.super_brick, &e.ms) == 18 &&
             check_launch(e.cfg) == GBD_OK)
             ctx.tuned[k] = e;  // later lines win
     }
@@ -204,7 +204,7 @@ int gbd_relayout(gbd_ctx *ctx, gbd_volume vid, int32_t brick, int32_t super_bric
     std::lock_guard<std::mutex> lock(ctx->mu);
     Volume *v = ctx->find(vid);
     if (!v) return fail(GBD_ERR_NOTFOUND, "unknown volume %llu", static_cast<unsigned long long>(vid));
-    if (v->pinned_by_requests > 0) return fail(GBD_ERR_BUSY, "volume has queued requests");
+    if (v->pinned_by_requests.load() > 0) return fail(GBD_ERR_BUSY, "volume has queued requests");
     DeviceGuard guard(ctx->device);
     return relayout_volume(*ctx, *v, vid, brick, super_brick);
 }
@@ -220,7 +220,7 @@ int gbd_tune(gbd_ctx *ctx, gbd_volume vid, const gbd_view *views, int32_t n, con
     std::lock_guard<std::mutex> lock(ctx->mu);
     Volume *vol = ctx->find(vid);
     if (!vol) return fail(GBD_ERR_NOTFOUND, "unknown volume %llu", static_cast<unsigned long long>(vid));
-    if ((what & GBD_TUNE_LAYOUT) && vol->pinned_by_requests > 0) return fail(GBD_ERR_BUSY, "volume has queued requests");
+    if ((what & GBD_TUNE_LAYOUT) && vol->pinned_by_requests.load() > 0) return fail(GBD_ERR_BUSY, "volume has queued requests");
     DeviceGuard guard(ctx->device);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     std::vector<ViewDev> hv(static_cast<size_t>(n));
@@ -228,30 +228,40 @@ int gbd_tune(gbd_ctx *ctx, gbd_volume vid, const gbd_view *views, int32_t n, con
     for (int k = 0; k < n; ++k)
         if ((rc = make_view(*vol, views[k], spec->width, spec->height, spec->fov_u, spec->fov_v, hv[k]))) return rc;
 
-    LaunchCfg best{8, 4, 8, 2, 1};
+    const bool verbose = std::getenv("GBD_TUNE_VERBOSE") != nullptr;
+    auto report = [&](const LaunchCfg &c, float ms, int B, int S) {
+        if (verbose)
+            std::fprintf(stderr, "gbd_tune: packet %2dx%-2d warps %d depth %d persistent %d regcap %d layout %d/%d: %.4f ms\n",
+                         c.packet_w, c.packet_h, c.cta_warps, c.depth, c.persistent, c.regcap, B, S, ms);
+    };
+    LaunchCfg best{8, 4, 8, 2, 1, 0};
     float best_ms = 0.f;
     int tried = 0;
     if ((rc = time_config(*ctx, *vol, hv, *spec, best, st, 3, best_ms))) return rc;
+    report(best, best_ms, vol->brick, vol->super_brick);
     ++tried;
     if (what & GBD_TUNE_LAUNCH) {
         const int packets[3][2] = {{8, 4}, {4, 8}, {16, 2}};
-        const int warps[2] = {4, 8};
+        const int warps[4] = {1, 2, 4, 8};
         const int depths[3] = {1, 2, 4};
-        for (const auto &pk : packets)
-            for (int w : warps)
-                for (int d : depths) {
-                    LaunchCfg c{pk[0], pk[1], w, d, 1};
-                    float ms = 0.f;
-                    if ((rc = time_config(*ctx, *vol, hv, *spec, c, st, 3, ms))) return rc;
-                    ++tried;
-                    if (ms < best_ms) {
-                        best_ms = ms;
-                        best = c;
+        for (int cap = 0; cap < 2; ++cap)
+            for (const auto &pk : packets)
+                for (int w : warps)
+                    for (int d : depths) {
+                        LaunchCfg c{pk[0], pk[1], w, d, 1, cap};
+                        float ms = 0.f;
+                        if ((rc = time_config(*ctx, *vol, hv, *spec, c, st, 3, ms))) return rc;
+                        report(c, ms, vol->brick, vol->super_brick);
+                        ++tried;
+                        if (ms < best_ms) {
+                            best_ms = ms;
+                            best = c;
+                        }
                     }
-                }
-        LaunchCfg flat{8, 4, 8, 2, 0};
+        LaunchCfg flat{8, 4, 8, 2, 0, 0};
         float ms = 0.f;
         if ((rc = time_config(*ctx, *vol, hv, *spec, flat, st, 3, ms))) return rc;
+        report(flat, ms, vol->brick, vol->super_brick);
         ++tried;
         if (ms < best_ms) {
             best_ms = ms;
@@ -265,6 +275,7 @@ int gbd_tune(gbd_ctx *ctx, gbd_volume vid, const gbd_view *views, int32_t n, con
             if ((rc = relayout_volume(*ctx, *vol, vid, ly[0], ly[1]))) return rc;
             float ms = 0.f;
             if ((rc = time_config(*ctx, *vol, hv, *spec, best, st, 3, ms))) return rc;
+            report(best, ms, ly[0], ly[1]);
             ++tried;
             if (ms < best_ms) {
                 best_ms = ms;
@@ -287,6 +298,7 @@ int gbd_tune(gbd_ctx *ctx, gbd_volume vid, const gbd_view *views, int32_t n, con
     out->launch.cta_warps = best.cta_warps;
     out->launch.depth = best.depth;
     out->launch.persistent = best.persistent;
+    out->launch.regcap = best.regcap;
     out->brick = vol->brick;
     out->super_brick = vol->super_brick;
     out->ms = best_ms;

@@ -57,7 +57,7 @@ class ImageSpec(ctypes.Structure):
 
 class Launch(ctypes.Structure):
     _fields_ = [("packet_w", ctypes.c_int32), ("packet_h", ctypes.c_int32), ("cta_warps", ctypes.c_int32),
-                ("depth", ctypes.c_int32), ("persistent", ctypes.c_int32)]
+                ("depth", ctypes.c_int32), ("persistent", ctypes.c_int32), ("regcap", ctypes.c_int32)]
 
 
 class TuneResult(ctypes.Structure):
@@ -66,6 +66,28 @@ class TuneResult(ctypes.Structure):
 
 
 TUNE_LAUNCH, TUNE_LAYOUT = 1, 2
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("volume", ctypes.c_uint64), ("view", CView), ("spec", ImageSpec), ("priority", ctypes.c_int32)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("queue_ms", ctypes.c_double), ("latency_ms", ctypes.c_double),
+                ("device_ms", ctypes.c_double)]
+
+
+class ServeConfig(ctypes.Structure):
+    _fields_ = [("max_waves", ctypes.c_int32), ("max_requests_per_wave", ctypes.c_int32),
+                ("max_requests_in_flight", ctypes.c_int32), ("request_budget_bytes", ctypes.c_uint64),
+                ("launch", Launch)]
+
+
+class ServeSummary(ctypes.Structure):
+    _fields_ = [("completed", ctypes.c_uint64), ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double),
+                ("max_ms", ctypes.c_double), ("requests_per_s", ctypes.c_double), ("waves", ctypes.c_uint64),
+                ("mean_requests_per_wave", ctypes.c_double), ("max_waves_in_flight", ctypes.c_int32),
+                ("pending", ctypes.c_int32), ("in_flight", ctypes.c_int32)]
 
 
 class VolumeDesc(ctypes.Structure):
@@ -91,6 +113,14 @@ _SIGNATURES = {
     "gbd_bounds_violations": ([ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
     "gbd_render_batch_noalloc": ([ctypes.c_void_p, ctypes.c_uint64, ctypes.POINTER(CView), ctypes.c_int32,
                                   ctypes.POINTER(ImageSpec), ctypes.POINTER(Launch), ctypes.c_void_p], ctypes.c_int),
+    "gbd_serve_start": ([ctypes.c_void_p, ctypes.POINTER(ServeConfig)], ctypes.c_int),
+    "gbd_serve_stop": ([ctypes.c_void_p], ctypes.c_int),
+    "gbd_submit": ([ctypes.c_void_p, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_uint64)], ctypes.c_int),
+    "gbd_poll": ([ctypes.c_void_p, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(Stats)],
+                 ctypes.c_int),
+    "gbd_wait": ([ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32, ctypes.POINTER(Stats)], ctypes.c_int),
+    "gbd_cancel": ([ctypes.c_void_p, ctypes.c_uint64], ctypes.c_int),
+    "gbd_serve_stats": ([ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(ServeSummary)], ctypes.c_int),
     "gbd_tune": ([ctypes.c_void_p, ctypes.c_uint64, ctypes.POINTER(CView), ctypes.c_int32,
                   ctypes.POINTER(ImageSpec), ctypes.c_uint32, ctypes.c_void_p, ctypes.POINTER(TuneResult)],
                  ctypes.c_int),
@@ -151,6 +181,7 @@ def _launch(launch) -> ctypes.POINTER(Launch) | None:
     lw.cta_warps = launch.get("cta_warps", 0)
     lw.depth = launch.get("depth", 0)
     lw.persistent = int(launch.get("persistent", 1))
+    lw.regcap = int(launch.get("regcap", 0))
     return ctypes.pointer(lw)
 
 
@@ -335,8 +366,8 @@ class Context:
                                            _stream_handle(stream), ctypes.byref(res)))
         lw = res.launch
         return dict(packet=(lw.packet_w, lw.packet_h), cta_warps=lw.cta_warps, depth=lw.depth,
-                    persistent=lw.persistent, brick=res.brick, super_brick=res.super_brick, ms=res.ms,
-                    candidates=res.candidates)
+                    persistent=lw.persistent, regcap=lw.regcap, brick=res.brick, super_brick=res.super_brick,
+                    ms=res.ms, candidates=res.candidates)
 
     def relayout(self, vol: int, brick: int, super_brick: int):
         _check(self.lib, self.lib.gbd_relayout(self.handle, int(vol), int(brick), int(super_brick)))
@@ -347,6 +378,71 @@ class Context:
         w = ctypes.c_int32()
         _check(self.lib, self.lib.gbd_bounds_violations(self.handle, ctypes.byref(w)))
         return int(w.value)
+
+    # -- serving
+    def serve_start(self, *, max_waves: int = 0, max_requests_per_wave: int = 0, max_requests_in_flight: int = 0,
+                    request_budget_bytes: int = 0, launch=None):
+        cfg = ServeConfig()
+        cfg.max_waves = int(max_waves)
+        cfg.max_requests_per_wave = int(max_requests_per_wave)
+        cfg.max_requests_in_flight = int(max_requests_in_flight)
+        cfg.request_budget_bytes = int(request_budget_bytes)
+        lp = _launch(launch)
+        if lp is not None:
+            cfg.launch = lp.contents
+        _check(self.lib, self.lib.gbd_serve_start(self.handle, ctypes.byref(cfg)))
+
+    def serve_stop(self):
+        _check(self.lib, self.lib.gbd_serve_stop(self.handle))
+        self._served = {}
+
+    def submit(self, vol: int, view, out, *, priority: int = 0) -> int:
+        """Queue a render of ``view`` into ``out`` (device tensor, or pinned
+        host tensor) [height][width]; returns the ticket.  ``out`` is kept
+        alive until the request is reported done."""
+        r = Request()
+        r.volume = int(vol)
+        r.view = _cview(view)
+        on_host = not (hasattr(out, "is_cuda") and out.is_cuda)
+        ptr = out.data_ptr() if hasattr(out, "data_ptr") else out.ctypes.data
+        r.spec = self._spec(view, ptr, None, on_host=on_host)
+        r.priority = int(priority)
+        t = ctypes.c_uint64()
+        _check(self.lib, self.lib.gbd_submit(self.handle, ctypes.byref(r), ctypes.byref(t)))
+        if not hasattr(self, "_served"):
+            self._served = {}
+        self._served[int(t.value)] = out
+        return int(t.value)
+
+    @staticmethod
+    def _stats(st: Stats) -> dict:
+        return dict(status=st.status, queue_ms=st.queue_ms, latency_ms=st.latency_ms, device_ms=st.device_ms)
+
+    def poll(self, ticket: int):
+        """(done, stats); raises GbdError if the request ended with an error."""
+        done = ctypes.c_int32()
+        st = Stats()
+        rc = self.lib.gbd_poll(self.handle, int(ticket), ctypes.byref(done), ctypes.byref(st))
+        if done.value:
+            getattr(self, "_served", {}).pop(int(ticket), None)
+        _check(self.lib, rc)
+        return bool(done.value), self._stats(st)
+
+    def wait(self, ticket: int, timeout_ms: int = 60000) -> dict:
+        st = Stats()
+        rc = self.lib.gbd_wait(self.handle, int(ticket), int(timeout_ms), ctypes.byref(st))
+        if rc != ERR_TIMEOUT:
+            getattr(self, "_served", {}).pop(int(ticket), None)
+        _check(self.lib, rc)
+        return self._stats(st)
+
+    def cancel(self, ticket: int):
+        _check(self.lib, self.lib.gbd_cancel(self.handle, int(ticket)))
+
+    def serve_stats(self, reset: bool = False) -> dict:
+        s = ServeSummary()
+        _check(self.lib, self.lib.gbd_serve_stats(self.handle, int(bool(reset)), ctypes.byref(s)))
+        return {k: getattr(s, k) for k, _ in ServeSummary._fields_}
 
     def last_launch_count(self) -> int:
         return int(self.lib.gbd_last_launch_count())
