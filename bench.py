@@ -55,14 +55,16 @@ def make_workload(name: str, scale: float = 1.0, device: str = "cpu"):
                 "step (theta in {10,45} deg x 9 observer times), retarded-time epoch lerp on")
         return dict(grid=grid, j=j, beta=beta, views=views, store="f32", desc=desc, lookback=True)
     if name == "precision":
-        grid, j, beta, views = gen.config_precision_device(device=device)
-        desc = ("precision: 512^3 grid x 8 epochs turbulent jet, stored bf16 j' + fp16 u=Gamma*beta, FP32 "
-                "accumulation; one 1024x1024 view at theta=30, phi=20, t_obs mid-window")
+        n, size = int(round(512 * scale)), int(round(1024 * scale))
+        grid, j, beta, views = gen.config_precision_device(n=n, size=size, device=device)
+        desc = (f"precision: {n}^3 grid x 8 epochs turbulent jet, stored bf16 j' + fp16 u=Gamma*beta, FP32 "
+                f"accumulation; one {size}x{size} view at theta=30, phi=20, t_obs mid-window")
         return dict(grid=grid, j=j, beta=beta, views=views, store="bf16", desc=desc, lookback=True)
     if name == "batched":
-        grid, j, beta, views = gen.config_batched_device(device=device)
-        desc = ("batched views: 384^3 grid x 32 epochs FP32 turbulent jet, 256 orientations on a Fibonacci "
-                "sphere, 256x256 each, one persistent graph-captured launch")
+        n, size = int(round(384 * scale)), int(round(256 * scale))
+        grid, j, beta, views = gen.config_batched_device(n=n, size=size, device=device)
+        desc = (f"batched views: {n}^3 grid x 32 epochs FP32 turbulent jet, 256 orientations on a Fibonacci "
+                f"sphere, {size}x{size} each, one persistent graph-captured launch")
         return dict(grid=grid, j=j, beta=beta, views=views, store="f32", desc=desc, lookback=True)
     raise SystemExit(f"unknown workload {name}")
 
@@ -177,7 +179,8 @@ def run_gpu(args, rank: int, world: int):
     n_views = len(views)
     ctx = Context(dev)
     t_load = time.perf_counter()
-    vol = ctx.load_snapshots(wl["grid"], wl["j"], wl["beta"], store=wl["store"])
+    brick, sbrick = (int(x) for x in args.layout.split(",")) if args.layout else (0, 0)
+    vol = ctx.load_snapshots(wl["grid"], wl["j"], wl["beta"], store=wl["store"], brick=brick, super_brick=sbrick)
     torch.cuda.synchronize()
     t_load = time.perf_counter() - t_load
     info = ctx.volume_info(vol)
@@ -190,7 +193,11 @@ def run_gpu(args, rank: int, world: int):
     stream = torch.cuda.Stream()
     launch = None
     tuned = None
-    if not args.no_tune:
+    if args.launch:
+        pw, ph, warps, depth, regcap = (int(x) for x in args.launch.split(","))
+        launch = {"packet": (pw, ph), "cta_warps": warps, "depth": depth, "persistent": 1, "regcap": regcap}
+        tuned = dict(launch)
+    elif not args.no_tune:
         # autotune the launch (and, with --tune-layout, the volume layout) before timing
         tuned = ctx.tune(vol, views, launch=True, layout=args.tune_layout, stream=stream)
         info = ctx.volume_info(vol)
@@ -288,6 +295,114 @@ def run_gpu(args, rank: int, world: int):
     return result, clk.summary(), wl
 
 
+# ------------------------------------------------------------------ serving
+SERVING_CATALOGUE = [  # (n, epochs, store)
+    (64, 32, "f32"), (128, 16, "bf16"), (256, 32, "f32"), (384, 8, "bf16"), (512, 8, "f32"), (512, 32, "bf16")]
+
+
+def run_serving(args, rank: int, world: int):
+    """Continuous batching under Poisson load: p50/p99 latency (submission to
+    completion on the GPU), throughput and cell-samples/s at 0.5, 0.8 and
+    0.95 of the saturated request rate."""
+    import torch
+    import gen
+    from paper_2609_09322_gb300 import Context
+
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    device = f"cuda:{dev}"
+    ctx = Context(dev)
+    vols, grids = [], []
+    t_load = time.perf_counter()
+    for k, (n, m, store) in enumerate(SERVING_CATALOGUE):
+        grid = gen.Grid(n=(n, n, n), n_epochs=m, t0=0.0, dt=n / 16.0)
+        j, beta = gen.turbulent_jet_torch(grid, 50 + k, device)
+        vols.append(ctx.load_snapshots(grid, j, beta, store=store))
+        grids.append(grid)
+        del j, beta
+        torch.cuda.empty_cache()
+    t_load = time.perf_counter() - t_load
+    resident = sum(ctx.volume_info(v)["bytes"] for v in vols)
+    rng = np.random.default_rng(args.seed)
+
+    def make_requests(count):
+        reqs = []
+        for _ in range(count):
+            k = int(rng.integers(len(vols)))
+            grid = grids[k]
+            size = int(rng.choice([128, 256, 512, 1024]))
+            d = rng.normal(size=3)
+            t_obs = float(rng.uniform(0.0, (grid.n_epochs - 1) * grid.dt))
+            reqs.append((vols[k], gen.view_from_direction(grid, -d, size=size, c=1.0, t_obs=t_obs)))
+        return reqs
+
+    reqs = make_requests(args.serve_requests + args.serve_warmup)
+    outs = [torch.empty((v.height, v.width), dtype=torch.float32, device=device) for _, v in reqs]
+    # cell-samples of every request, counted once outside the timed phases
+    samples = []
+    for vol, view in reqs:
+        _, cnt = ctx.render(vol, view, samples=True)
+        samples.append(cnt)
+    torch.cuda.synchronize()
+    samples = [int(c.to(torch.int64).sum().item()) for c in samples]
+    ctx.serve_start(max_waves=args.serve_waves, max_requests_per_wave=args.serve_wave_size)
+
+    def run_phase(rate, lo, hi):
+        """Submit requests lo..hi-1 (Poisson at `rate` per second, or all at
+        once when rate is None); returns stats of the measured part."""
+        ctx.serve_stats(reset=True)
+        tickets = []
+        t = time.perf_counter()
+        next_t = t
+        warm = min(args.serve_warmup, hi - lo)
+        for i in range(lo, hi):
+            if rate:
+                next_t += float(rng.exponential(1.0 / rate))
+                while time.perf_counter() < next_t:
+                    pass
+            if i == lo + warm:
+                for tk in tickets:
+                    ctx.wait(tk, 120000)
+                tickets = []
+                ctx.serve_stats(reset=True)
+                t_meas = time.perf_counter()
+                s_meas = 0
+            tickets.append(ctx.submit(reqs[i][0], reqs[i][1], outs[i]))
+            if i >= lo + warm:
+                s_meas += samples[i]
+        for tk in tickets:
+            ctx.wait(tk, 120000)
+        st = ctx.serve_stats()
+        span = time.perf_counter() - t_meas
+        return dict(offered_per_s=round(rate, 1) if rate else None, completed=st["completed"],
+                    p50_ms=round(st["p50_ms"], 3), p99_ms=round(st["p99_ms"], 3), max_ms=round(st["max_ms"], 3),
+                    requests_per_s=round(st["completed"] / span, 1),
+                    gcell_samples_per_s=round(s_meas / span / 1e9, 3),
+                    mean_requests_per_wave=round(st["mean_requests_per_wave"], 2),
+                    max_waves_in_flight=st["max_waves_in_flight"])
+
+    total = len(reqs)
+    sat = run_phase(None, 0, total)
+    r_sat = sat["requests_per_s"]
+    points = [run_phase(f * r_sat, 0, total) for f in (0.5, 0.8, 0.95)]
+    top = points[-1]
+    result = {
+        "metric": METRIC, "value": top["gcell_samples_per_s"], "unit": UNIT, "n_gpus": world,
+        "steps": args.serve_requests, "warmup": args.serve_warmup, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32 / bf16+f16 storage, f32 math", "data": "synthetic (seeded generators in gen/)",
+        "config": {"workload": "serving: Poisson stream of render requests over a resident catalogue of "
+                               + ", ".join(f"{n}^3x{m} {st}" for n, m, st in SERVING_CATALOGUE)
+                               + "; images 128^2-1024^2, random orientations and observer times",
+                   "resident_bytes": resident, "max_waves": args.serve_waves,
+                   "max_requests_per_wave": args.serve_wave_size},
+        "serving": {"saturated": sat, "load_points": points},
+        "p50_ms": top["p50_ms"], "p99_ms": top["p99_ms"],
+        "load_s": round(t_load, 1),
+    }
+    ctx.close()
+    return result
+
+
 # ------------------------------------------------------------------ CPU oracle
 def oracle_sample(wl, seconds: float, seed: int = 0):
     """Times the oracle on a random sample of the workload's pixels until
@@ -344,14 +459,21 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="gbdart", choices=["gbdart", "reference"])
-    ap.add_argument("--workload", default="time_delay", choices=["time_delay", "precision", "batched"])
+    ap.add_argument("--workload", default="time_delay", choices=["time_delay", "precision", "batched", "serving"])
+    ap.add_argument("--serve-requests", type=int, default=2000)
+    ap.add_argument("--serve-warmup", type=int, default=200)
+    ap.add_argument("--serve-waves", type=int, default=3)
+    ap.add_argument("--serve-wave-size", type=int, default=64)
+    ap.add_argument("--seed", type=int, default=5)
     ap.add_argument("--scale", type=float, default=1.0,
-                    help="linear size factor of the time_delay workload (1 = the stated configuration; "
-                         "smaller cases are for profiling)")
+                    help="linear size factor of the workload's grid and images (1 = the stated "
+                         "configuration; smaller cases are for profiling)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="oracle work for the cpu_baseline key")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="skip the launch autotuner (default configuration)")
     ap.add_argument("--tune-layout", action="store_true", help="also autotune the volume's brick layout")
+    ap.add_argument("--launch", default="", help="fixed launch instead of tuning: packet_w,packet_h,warps,depth,regcap")
+    ap.add_argument("--layout", default="", help="fixed volume layout: brick,super_brick")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
@@ -366,6 +488,10 @@ def main():
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
+    if args.workload == "serving":
+        if rank == 0:
+            print(json.dumps(run_serving(args, rank, world)), flush=True)
+        return
     result, clocks, wl = run_gpu(args, rank, world)
     result["clocks"] = clocks
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -118,6 +118,10 @@ typedef struct {
     int32_t on_device;
     int32_t brick;       /* layout: brick edge 4 or 8; 0 = library default  */
     int32_t super_brick; /* bricks per super-brick edge 1, 2 or 4; 0 = default */
+    int32_t paired;      /* 1: keep the records of snapshots m and m + 1 of
+                            each cell side by side (M + 1 blocks), so a cell
+                            sample under lookback is one contiguous load;
+                            costs about 2 (M + 1) / M times the memory      */
 } gbd_fields;
 
 /* One observation (Secs. 2.1-2.2, 2.5). */
@@ -161,7 +165,7 @@ typedef struct {
 typedef struct {
     gbd_grid grid;
     int32_t store;
-    int32_t brick, super_brick;
+    int32_t brick, super_brick, paired;
     uint64_t bytes;          /* device bytes held by the packed volume       */
     uint64_t record_bytes;   /* 16 (F32) or 8 (BF16_F16U)                    */
 } gbd_volume_desc;
@@ -324,8 +328,9 @@ typedef struct {
 /* Times candidate configurations for rendering `views` (as gbd_render_batch
  * would, writing into spec->out, which must be device memory) on `stream`
  * and synchronises it.  With GBD_TUNE_LAYOUT the volume is re-packed on the
- * device into each candidate layout and left in the fastest one (the handle
- * stays valid; the re-pack needs room for a second copy within the budget).
+ * device into each candidate layout (bricks, and the paired-snapshot form when
+ * it fits) and left in the fastest one (the handle stays valid; the re-pack
+ * needs room for a second copy within the budget).
  * The best launch configuration is remembered by the context and used by
  * gbd_render and gbd_render_batch calls of the same class that pass
  * launch = NULL.  With the environment variable GBD_TUNE_CACHE naming a file,
@@ -334,8 +339,9 @@ int gbd_tune(gbd_ctx *ctx, gbd_volume vol, const gbd_view *views, int32_t n, con
              uint32_t what, void *stream, gbd_tune_result *out);
 
 /* Re-packs a volume into another layout on the device (brick 1, 2, 4 or 8;
- * super_brick 1, 2 or 4), keeping its handle.  Waits for the device. */
-int gbd_relayout(gbd_ctx *ctx, gbd_volume vol, int32_t brick, int32_t super_brick);
+ * super_brick 1, 2 or 4; paired 0 or 1), keeping its handle.  Waits for the
+ * device.  Needs room for both copies within the budget while it runs. */
+int gbd_relayout(gbd_ctx *ctx, gbd_volume vol, int32_t brick, int32_t super_brick, int32_t paired);
 
 /* Bounds checking.  In the library built with GBD_CHECKED every gather tests
  * its cell and epoch index against the volume; a violation skips the load and

@@ -203,6 +203,14 @@ int make_view(const Volume &vol, const gbd_view &v, int width, int height, doubl
     return GBD_OK;
 }
 
+// Record bytes of a packed volume; *stride receives the records per block.
+size_t volume_bytes(int store, long long cells_per_epoch, int M, int paired, long long *stride)
+{
+    const size_t rec = store == GBD_STORE_F32 ? 16 : 8;
+    *stride = paired ? 2 * cells_per_epoch : cells_per_epoch;
+    return rec * static_cast<size_t>(*stride) * static_cast<size_t>(paired ? M + 1 : M);
+}
+
 VolDev vol_dev(const Volume &v)
 {
     VolDev d;
@@ -213,6 +221,7 @@ VolDev vol_dev(const Volume &v)
     for (int i = 0; i < 3; ++i) d.n[i] = v.grid.n[i];
     d.M = v.grid.n_epochs;
     d.store = v.store;
+    d.paired = v.paired;
     return d;
 }
 
@@ -579,11 +588,13 @@ int gbd_load_snapshots(gbd_ctx *ctx, const gbd_grid *grid, const gbd_fields *f, 
     vol->store = f->store;
     vol->brick = B;
     vol->super_brick = S;
+    vol->paired = f->paired ? 1 : 0;
     std::vector<int32_t> tab;
-    if (!build_layout(g.n, B, S, tab, vol->epoch_stride))
+    long long cells = 0;
+    if (!build_layout(g.n, B, S, tab, cells) || (vol->paired && 2 * cells >= (1LL << 31)))
         return fail(GBD_ERR_INVALID, "grid too large: one epoch exceeds 2^31 records");
     const size_t rec_bytes = f->store == GBD_STORE_F32 ? 16 : 8;
-    const size_t bytes = rec_bytes * static_cast<size_t>(vol->epoch_stride) * g.n_epochs;
+    const size_t bytes = volume_bytes(f->store, cells, g.n_epochs, vol->paired, &vol->epoch_stride);
     const size_t tab_bytes = tab.size() * sizeof(int32_t);
     if (ctx->used + bytes + tab_bytes > ctx->budget)
         return fail(GBD_ERR_BUDGET, "volume needs %zu bytes, %llu of %llu budget in use", bytes + tab_bytes,
@@ -629,7 +640,10 @@ int gbd_load_snapshots(gbd_ctx *ctx, const gbd_grid *grid, const gbd_fields *f, 
         pa.store = f->store;
         for (int i = 0; i < 3; ++i) pa.n[i] = g.n[i];
         pa.axis_off = vol->axis_off;
-        pa.dst = static_cast<char *>(vol->rec) + static_cast<size_t>(m) * vol->epoch_stride * rec_bytes;
+        pa.dst = vol->rec;
+        pa.stride = vol->epoch_stride;
+        pa.m = m;
+        pa.paired = vol->paired;
         pa.bad = bad;
         if (e == cudaSuccess) e = launch_pack(pa, st);
         // The host staging buffer is reused for the next epoch only after
@@ -684,6 +698,7 @@ int gbd_volume_info(gbd_ctx *ctx, gbd_volume vid, gbd_volume_desc *out)
     out->store = v->store;
     out->brick = v->brick;
     out->super_brick = v->super_brick;
+    out->paired = v->paired;
     out->bytes = v->bytes;
     out->record_bytes = v->store == GBD_STORE_F32 ? 16 : 8;
     return GBD_OK;

@@ -22,10 +22,11 @@ constexpr int kMaxAxis = 4096;
 struct VolDev {
     const void *rec;          // record array (16-byte or 8-byte records)
     const int32_t *axis_off;  // n[0] + n[1] + n[2] entries
-    long long epoch_stride;   // records per epoch (padded)
+    long long epoch_stride;   // records per block (padded)
     int n[3];
     int M;
     int store;                // GBD_STORE_*
+    int paired;               // 1: block b holds snapshots b-1 and b side by side
 };
 
 // Per-view constants, computed on the host in float64 once per view, so that
@@ -111,16 +112,22 @@ struct PackArgs {
     int store;                // GBD_STORE_*
     int n[3];
     const int32_t *axis_off;  // device tables
-    void *dst;                // records of this epoch
+    void *dst;                // the whole record array
+    long long stride;         // records per block
+    int m;                    // epoch being packed
+    int paired;               // write into blocks m (second slot) and m + 1 (first slot)
     int *bad;                 // device flag: set to 1 on an invalid value
 };
 cudaError_t launch_pack(const PackArgs &a, cudaStream_t stream);
 
 struct RelayoutArgs {
-    const void *src;          // records of one epoch in the old layout
-    void *dst;                // records of the same epoch in the new layout
+    const void *src;          // whole record array in the old layout
+    void *dst;                // whole record array in the new layout
     const int32_t *src_off;   // per-axis tables of the old layout
     const int32_t *dst_off;   // per-axis tables of the new layout
+    long long src_stride, dst_stride;  // records per block
+    int src_paired, dst_paired;
+    int m;                    // epoch being copied
     int n[3];
     int record_bytes;         // 16 or 8
 };

@@ -70,6 +70,13 @@ struct Record<GBD_STORE_F32> {
         return __ldg(reinterpret_cast<const float4 *>(base) + off);
     }
     static __device__ __forceinline__ T zero() { return make_float4(0.f, 0.f, 0.f, 0.f); }
+    // Both snapshots of a paired block: 32 contiguous bytes.
+    static __device__ __forceinline__ void load_pair(const void *base, long long off, T &lo, T &hi)
+    {
+        const float4 *p = reinterpret_cast<const float4 *>(base) + off;
+        lo = __ldg(p);
+        hi = __ldg(p + 1);
+    }
     // D^(2 - alpha) j' with D = sqrt(1 - beta^2) / (1 + beta . s_hat) (Eq. 14).
     // 1 + beta.s_hat and 1 - beta^2 are formed with fused multiply-adds so
     // each is rounded once near its (possibly small) value.
@@ -93,6 +100,13 @@ struct Record<GBD_STORE_BF16_F16U> {
         return __ldg(reinterpret_cast<const uint2 *>(base) + off);
     }
     static __device__ __forceinline__ T zero() { return make_uint2(0u, 0u); }
+    // Both snapshots of a paired block: one 16-byte load (off is even).
+    static __device__ __forceinline__ void load_pair(const void *base, long long off, T &lo, T &hi)
+    {
+        const uint4 v = __ldg(reinterpret_cast<const uint4 *>(base) + (off >> 1));
+        lo = make_uint2(v.x, v.y);
+        hi = make_uint2(v.z, v.w);
+    }
     // D = 1 / (Gamma + u.s_hat).  When u.s_hat < 0 (motion towards the
     // observer) the denominator cancels, so the same D is evaluated as
     // (Gamma + |u.s_hat|) / (1 + |u|^2 - (u.s_hat)^2), which has no cancellation.
@@ -151,7 +165,7 @@ __device__ __forceinline__ float fix_to_float(long long v, float inv_scale)
 
 // Marches the ray of pixel (p, q) of one image and stores its value (and,
 // if cnt_img is set, its cell-sample count).  out_img points at the image.
-template <int STORE, int DEPTH>
+template <int STORE, int DEPTH, bool PAIRED>
 __device__ __forceinline__ void march_ray(const VolDev &vol, const ViewDev &V, int p, int q, int width, int height,
                                           float *out_img, uint32_t *cnt_img, int *err_word,
                                           const int32_t *__restrict__ offx, const int32_t *__restrict__ offy,
@@ -303,12 +317,15 @@ __device__ __forceinline__ void march_ray(const VolDev &vol, const ViewDev &V, i
                         has_lo[d] = has_hi[d] = false;
                     }
 #endif
-                    off[d] = static_cast<long long>(mb) * es + (ox + oy + oz);
+                    // unpaired: snapshot m at block m; paired: snapshots mb and
+                    // mb + 1 side by side in block mb + 1
+                    off[d] = PAIRED ? static_cast<long long>(mb + 1) * es + 2LL * (ox + oy + oz)
+                                    : static_cast<long long>(mb) * es + (ox + oy + oz);
                     wgt[d] = w;
                     dsv[d] = ds;
                 }
-                // Past the last time that reaches a snapshot: nothing further
-                // along the ray can contribute.
+                // Past the last time that reaches a snapshot, or out of the
+                // box: nothing further along the ray can contribute.
                 if (u_exit <= u_lo || s_exit >= s_hi_box || --steps_left <= 0) {
                     alive = false;
                 } else if (x0) {
@@ -360,8 +377,14 @@ __device__ __forceinline__ void march_ray(const VolDev &vol, const ViewDev &V, i
         typename Rec::T rlo[DEPTH], rhi[DEPTH];
 #pragma unroll
         for (int d = 0; d < DEPTH; ++d) {
-            rlo[d] = has_lo[d] ? Rec::load(recs, off[d]) : Rec::zero();
-            rhi[d] = has_hi[d] ? Rec::load(recs, off[d] + es) : Rec::zero();
+            if (PAIRED) {
+                rlo[d] = Rec::zero();
+                rhi[d] = Rec::zero();
+                if (has_lo[d] || has_hi[d]) Rec::load_pair(recs, off[d], rlo[d], rhi[d]);
+            } else {
+                rlo[d] = has_lo[d] ? Rec::load(recs, off[d]) : Rec::zero();
+                rhi[d] = has_hi[d] ? Rec::load(recs, off[d] + es) : Rec::zero();
+            }
         }
 #pragma unroll
         for (int d = 0; d < DEPTH; ++d) {
@@ -387,7 +410,7 @@ __device__ __forceinline__ void march_ray(const VolDev &vol, const ViewDev &V, i
 
 // MINB = 1 leaves the register count to the compiler; MINB = 3 asks for
 // three 256-thread CTAs per SM (at most 80 registers per thread).
-template <int STORE, int DEPTH, int MINB>
+template <int STORE, int DEPTH, int MINB, bool PAIRED>
 __global__ void __launch_bounds__(256, MINB) march_kernel(const MarchArgs a)
 {
     extern __shared__ int32_t s_off[];
@@ -418,8 +441,8 @@ __global__ void __launch_bounds__(256, MINB) march_kernel(const MarchArgs a)
         const int p = tx * a.packet_w + lane % a.packet_w;
         const int q = ty * a.packet_h + lane / a.packet_w;
         const long long img = static_cast<long long>(vi) * a.width * a.height;
-        march_ray<STORE, DEPTH>(a.vol, a.views[vi], p, q, a.width, a.height, a.out + img,
-                                a.samples ? a.samples + img : nullptr, a.error_word, offx, offy, offz);
+        march_ray<STORE, DEPTH, PAIRED>(a.vol, a.views[vi], p, q, a.width, a.height, a.out + img,
+                                        a.samples ? a.samples + img : nullptr, a.error_word, offx, offy, offz);
         if (!a.persistent) break;
     }
 }
@@ -453,37 +476,54 @@ __global__ void __launch_bounds__(256, MINB) wave_kernel(const WaveArgs a)
         const int32_t *tab = R.vol.axis_off;
         const int32_t *ty_tab = tab + R.vol.n[0];
         const int32_t *tz_tab = ty_tab + R.vol.n[1];
-        if (R.vol.store == GBD_STORE_F32)
-            march_ray<GBD_STORE_F32, DEPTH>(R.vol, R.view, p, q, R.width, R.height, R.out, R.samples, a.error_word,
-                                            tab, ty_tab, tz_tab);
-        else
-            march_ray<GBD_STORE_BF16_F16U, DEPTH>(R.vol, R.view, p, q, R.width, R.height, R.out, R.samples,
-                                                  a.error_word, tab, ty_tab, tz_tab);
+        if (R.vol.store == GBD_STORE_F32) {
+            if (R.vol.paired)
+                march_ray<GBD_STORE_F32, DEPTH, true>(R.vol, R.view, p, q, R.width, R.height, R.out, R.samples,
+                                                      a.error_word, tab, ty_tab, tz_tab);
+            else
+                march_ray<GBD_STORE_F32, DEPTH, false>(R.vol, R.view, p, q, R.width, R.height, R.out, R.samples,
+                                                       a.error_word, tab, ty_tab, tz_tab);
+        } else {
+            if (R.vol.paired)
+                march_ray<GBD_STORE_BF16_F16U, DEPTH, true>(R.vol, R.view, p, q, R.width, R.height, R.out,
+                                                            R.samples, a.error_word, tab, ty_tab, tz_tab);
+            else
+                march_ray<GBD_STORE_BF16_F16U, DEPTH, false>(R.vol, R.view, p, q, R.width, R.height, R.out,
+                                                             R.samples, a.error_word, tab, ty_tab, tz_tab);
+        }
     }
 }
 
-template <int STORE, int DEPTH, int MINB>
+template <int STORE, int DEPTH, int MINB, bool PAIRED>
 void *kernel_ptr()
 {
-    return reinterpret_cast<void *>(&march_kernel<STORE, DEPTH, MINB>);
+    return reinterpret_cast<void *>(&march_kernel<STORE, DEPTH, MINB, PAIRED>);
 }
 
-template <int STORE, int MINB>
+template <int STORE, int MINB, bool PAIRED>
 void *select_depth(int depth)
 {
     switch (depth) {
-    case 1: return kernel_ptr<STORE, 1, MINB>();
-    case 2: return kernel_ptr<STORE, 2, MINB>();
-    case 4: return kernel_ptr<STORE, 4, MINB>();
+    case 1: return kernel_ptr<STORE, 1, MINB, PAIRED>();
+    case 2: return kernel_ptr<STORE, 2, MINB, PAIRED>();
+    case 4: return kernel_ptr<STORE, 4, MINB, PAIRED>();
     default: return nullptr;
     }
 }
 
-void *select_kernel(int store, int depth, int capped)
+template <int STORE, bool PAIRED>
+void *select_cap(int depth, int capped)
 {
-    if (store == GBD_STORE_F32) return capped ? select_depth<GBD_STORE_F32, 3>(depth) : select_depth<GBD_STORE_F32, 1>(depth);
+    return capped ? select_depth<STORE, 3, PAIRED>(depth) : select_depth<STORE, 1, PAIRED>(depth);
+}
+
+void *select_kernel(int store, int depth, int capped, int paired)
+{
+    if (store == GBD_STORE_F32)
+        return paired ? select_cap<GBD_STORE_F32, true>(depth, capped) : select_cap<GBD_STORE_F32, false>(depth, capped);
     if (store == GBD_STORE_BF16_F16U)
-        return capped ? select_depth<GBD_STORE_BF16_F16U, 3>(depth) : select_depth<GBD_STORE_BF16_F16U, 1>(depth);
+        return paired ? select_cap<GBD_STORE_BF16_F16U, true>(depth, capped)
+                      : select_cap<GBD_STORE_BF16_F16U, false>(depth, capped);
     return nullptr;
 }
 
@@ -516,14 +556,14 @@ cudaError_t launch_wave(const WaveArgs &a, const LaunchCfg &cfg, int num_sms, cu
 
 cudaError_t march_occupancy(const LaunchCfg &cfg, int store, int smem_bytes, int *blocks_per_sm)
 {
-    void *k = select_kernel(store, cfg.depth, cfg.regcap);
+    void *k = select_kernel(store, cfg.depth, cfg.regcap, 0);
     if (!k) return cudaErrorInvalidValue;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k, 32 * cfg.cta_warps, smem_bytes);
 }
 
 cudaError_t launch_march(const MarchArgs &a, const LaunchCfg &cfg, int num_sms, cudaStream_t stream)
 {
-    void *k = select_kernel(a.vol.store, cfg.depth, cfg.regcap);
+    void *k = select_kernel(a.vol.store, cfg.depth, cfg.regcap, a.vol.paired);
     if (!k) return cudaErrorInvalidValue;
     const int threads = 32 * cfg.cta_warps;
     const int smem = static_cast<int>(sizeof(int32_t)) * (a.vol.n[0] + a.vol.n[1] + a.vol.n[2]);

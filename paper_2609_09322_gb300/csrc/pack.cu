@@ -42,7 +42,12 @@ __global__ void pack_kernel(const PackArgs a)
         const long long r = i / nx;
         const int iy = static_cast<int>(r % ny);
         const int iz = static_cast<int>(r / ny);
-        const long long off = static_cast<long long>(offx[ix]) + offy[iy] + offz[iz];
+        const long long cell = static_cast<long long>(offx[ix]) + offy[iy] + offz[iz];
+        // paired blocks: snapshot m is the second record of block m and the
+        // first record of block m + 1
+        const long long off = a.paired ? static_cast<long long>(a.m) * a.stride + 2 * cell + 1
+                                       : static_cast<long long>(a.m) * a.stride + cell;
+        const long long off2 = off + a.stride - 1;
         const double j = ld(jin, i);
         const double bx = ld(vin, 3 * i), by = ld(vin, 3 * i + 1), bz = ld(vin, 3 * i + 2);
         bool ok = isfinite(j) && j >= 0.0 && isfinite(bx) && isfinite(by) && isfinite(bz);
@@ -53,7 +58,9 @@ __global__ void pack_kernel(const PackArgs a)
             // rounding of 1 - beta^2.
             const double b2 = static_cast<double>(fx) * fx + static_cast<double>(fy) * fy + static_cast<double>(fz) * fz;
             ok = ok && isfinite(jf) && b2 <= 1.0 - 1.0 / 1048576.0;
-            reinterpret_cast<float4 *>(a.dst)[off] = ok ? make_float4(jf, fx, fy, fz) : make_float4(0.f, 0.f, 0.f, 0.f);
+            const float4 rec = ok ? make_float4(jf, fx, fy, fz) : make_float4(0.f, 0.f, 0.f, 0.f);
+            reinterpret_cast<float4 *>(a.dst)[off] = rec;
+            if (a.paired) reinterpret_cast<float4 *>(a.dst)[off2] = rec;
         } else {
             const double b2 = __dadd_rn(__dadd_rn(__dmul_rn(bx, bx), __dmul_rn(by, by)), __dmul_rn(bz, bz));
             ok = ok && b2 < 1.0;
@@ -66,7 +73,9 @@ __global__ void pack_kernel(const PackArgs a)
             uint2 rec;
             rec.x = static_cast<uint32_t>(__bfloat16_as_ushort(jb)) | (static_cast<uint32_t>(__half_as_ushort(ux)) << 16);
             rec.y = static_cast<uint32_t>(__half_as_ushort(uy)) | (static_cast<uint32_t>(__half_as_ushort(uz)) << 16);
-            reinterpret_cast<uint2 *>(a.dst)[off] = ok ? rec : make_uint2(0u, 0u);
+            if (!ok) rec = make_uint2(0u, 0u);
+            reinterpret_cast<uint2 *>(a.dst)[off] = rec;
+            if (a.paired) reinterpret_cast<uint2 *>(a.dst)[off2] = rec;
         }
         if (!ok) atomicExch(a.bad, 1);
     }
@@ -87,9 +96,17 @@ __global__ void relayout_kernel(const RelayoutArgs a)
         const long long r = i / nx;
         const int iy = static_cast<int>(r % ny);
         const int iz = static_cast<int>(r / ny);
-        const long long from = static_cast<long long>(a.src_off[ix]) + a.src_off[nx + iy] + a.src_off[nx + ny + iz];
-        const long long to = static_cast<long long>(a.dst_off[ix]) + a.dst_off[nx + iy] + a.dst_off[nx + ny + iz];
-        dst[to] = src[from];
+        const long long cs = static_cast<long long>(a.src_off[ix]) + a.src_off[nx + iy] + a.src_off[nx + ny + iz];
+        const long long cd = static_cast<long long>(a.dst_off[ix]) + a.dst_off[nx + iy] + a.dst_off[nx + ny + iz];
+        const long long from = a.src_paired ? static_cast<long long>(a.m) * a.src_stride + 2 * cs + 1
+                                            : static_cast<long long>(a.m) * a.src_stride + cs;
+        const R v = src[from];
+        if (a.dst_paired) {
+            dst[static_cast<long long>(a.m) * a.dst_stride + 2 * cd + 1] = v;
+            dst[static_cast<long long>(a.m + 1) * a.dst_stride + 2 * cd] = v;
+        } else {
+            dst[static_cast<long long>(a.m) * a.dst_stride + cd] = v;
+        }
     }
 }
 

@@ -20,9 +20,10 @@ struct Volume {
     gbd_grid grid{};
     int store = GBD_STORE_F32;
     int brick = 8, super_brick = 4;
-    void *rec = nullptr;             // records, epoch after epoch
+    int paired = 0;                  // blocks of side-by-side snapshot pairs
+    void *rec = nullptr;             // records, block after block
     int32_t *axis_off = nullptr;     // per-axis offset tables (n_x + n_y + n_z)
-    long long epoch_stride = 0;      // records per epoch
+    long long epoch_stride = 0;      // records per block (epoch, or epoch pair)
     uint64_t bytes = 0;              // device bytes charged to the budget
     std::atomic<int> pinned_by_requests{0};  // queued or running serving requests using it
 };
@@ -107,7 +108,8 @@ int render_direct(Ctx &ctx, const Volume &vol, const std::vector<ViewDev> &hv, c
 TuneKey tune_key(const Volume &vol, int width, int height, int n_views, uint32_t flags);
 bool lookup_tuned(Ctx &ctx, const TuneKey &k, LaunchCfg &cfg);
 void load_tune_file(Ctx &ctx);
-int relayout_volume(Ctx &ctx, Volume &vol, gbd_volume vid, int B, int S);
+int relayout_volume(Ctx &ctx, Volume &vol, gbd_volume vid, int B, int S, int paired);
+size_t volume_bytes(int store, long long cells_per_epoch, int M, int paired, long long *stride);
 
 // Serving (serve.cpp).
 int serve_start(Ctx &ctx, const gbd_serve_config *c);

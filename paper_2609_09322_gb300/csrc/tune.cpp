@@ -103,14 +103,16 @@ int time_config(Ctx &ctx, const Volume &vol, const std::vector<ViewDev> &hv, con
 // Re-packs a volume into another brick / super-brick layout on the device.
 // The handle keeps its identity; cached graphs of the volume are dropped
 // because their kernel parameters point at the old records.
-int relayout_volume(Ctx &ctx, Volume &vol, gbd_volume vid, int B, int S)
+int relayout_volume(Ctx &ctx, Volume &vol, gbd_volume vid, int B, int S, int paired)
 {
-    if (B == vol.brick && S == vol.super_brick) return GBD_OK;
+    paired = paired ? 1 : 0;
+    if (B == vol.brick && S == vol.super_brick && paired == vol.paired) return GBD_OK;
     std::vector<int32_t> tab;
-    long long stride = 0;
-    if (!build_layout(vol.grid.n, B, S, tab, stride)) return fail(GBD_ERR_INVALID, "layout too large");
+    long long cells = 0, stride = 0;
+    if (!build_layout(vol.grid.n, B, S, tab, cells) || (paired && 2 * cells >= (1LL << 31)))
+        return fail(GBD_ERR_INVALID, "layout too large");
     const size_t rec_bytes = vol.store == GBD_STORE_F32 ? 16 : 8;
-    const size_t bytes = rec_bytes * static_cast<size_t>(stride) * vol.grid.n_epochs;
+    const size_t bytes = volume_bytes(vol.store, cells, vol.grid.n_epochs, paired, &stride);
     const size_t tab_bytes = tab.size() * sizeof(int32_t);
     if (ctx.used + bytes + tab_bytes > ctx.budget)
         return fail(GBD_ERR_BUDGET, "re-layout needs %zu more bytes", bytes + tab_bytes);
@@ -129,8 +131,13 @@ int relayout_volume(Ctx &ctx, Volume &vol, gbd_volume vid, int B, int S)
     for (int m = 0; m < vol.grid.n_epochs && e == cudaSuccess; ++m) {
         RelayoutArgs ra;
         std::memset(&ra, 0, sizeof(ra));
-        ra.src = static_cast<const char *>(vol.rec) + static_cast<size_t>(m) * vol.epoch_stride * rec_bytes;
-        ra.dst = static_cast<char *>(rec) + static_cast<size_t>(m) * stride * rec_bytes;
+        ra.src = vol.rec;
+        ra.dst = rec;
+        ra.src_stride = vol.epoch_stride;
+        ra.dst_stride = stride;
+        ra.src_paired = vol.paired;
+        ra.dst_paired = paired;
+        ra.m = m;
         ra.src_off = vol.axis_off;
         ra.dst_off = off;
         for (int i = 0; i < 3; ++i) ra.n[i] = vol.grid.n[i];
@@ -154,6 +161,7 @@ int relayout_volume(Ctx &ctx, Volume &vol, gbd_volume vid, int B, int S)
     vol.epoch_stride = stride;
     vol.brick = B;
     vol.super_brick = S;
+    vol.paired = paired;
     vol.bytes = bytes + tab_bytes;
     ctx.used += vol.bytes;
     return GBD_OK;
@@ -195,7 +203,7 @@ using namespace gbd;
 
 extern "C" {
 
-int gbd_relayout(gbd_ctx *ctx, gbd_volume vid, int32_t brick, int32_t super_brick)
+int gbd_relayout(gbd_ctx *ctx, gbd_volume vid, int32_t brick, int32_t super_brick, int32_t paired)
 {
     if (!ctx) return fail(GBD_ERR_INVALID, "ctx is NULL");
     if (brick != 1 && brick != 2 && brick != 4 && brick != 8) return fail(GBD_ERR_INVALID, "brick must be 1, 2, 4 or 8");
@@ -206,7 +214,8 @@ int gbd_relayout(gbd_ctx *ctx, gbd_volume vid, int32_t brick, int32_t super_bric
     if (!v) return fail(GBD_ERR_NOTFOUND, "unknown volume %llu", static_cast<unsigned long long>(vid));
     if (v->pinned_by_requests.load() > 0) return fail(GBD_ERR_BUSY, "volume has queued requests");
     DeviceGuard guard(ctx->device);
-    return relayout_volume(*ctx, *v, vid, brick, super_brick);
+    if (paired != 0 && paired != 1) return fail(GBD_ERR_INVALID, "paired must be 0 or 1");
+    return relayout_volume(*ctx, *v, vid, brick, super_brick, paired);
 }
 
 int gbd_tune(gbd_ctx *ctx, gbd_volume vid, const gbd_view *views, int32_t n, const gbd_image_spec *spec,
@@ -270,20 +279,30 @@ int gbd_tune(gbd_ctx *ctx, gbd_volume vid, const gbd_view *views, int32_t n, con
     }
     if (what & GBD_TUNE_LAYOUT) {
         const int layouts[6][2] = {{8, 4}, {8, 2}, {8, 1}, {4, 4}, {4, 2}, {1, 1}};
-        int bestB = vol->brick, bestS = vol->super_brick;
-        for (const auto &ly : layouts) {
-            if ((rc = relayout_volume(*ctx, *vol, vid, ly[0], ly[1]))) return rc;
-            float ms = 0.f;
-            if ((rc = time_config(*ctx, *vol, hv, *spec, best, st, 3, ms))) return rc;
-            report(best, ms, ly[0], ly[1]);
-            ++tried;
-            if (ms < best_ms) {
-                best_ms = ms;
-                bestB = ly[0];
-                bestS = ly[1];
+        int bestB = vol->brick, bestS = vol->super_brick, bestP = vol->paired;
+        for (int pair = 0; pair < 2; ++pair) {
+            // the paired form is tried when two copies of it fit the budget
+            long long cells = 0, stride = 0;
+            std::vector<int32_t> tab;
+            build_layout(vol->grid.n, 8, 4, tab, cells);
+            if (pair && (vol->grid.n_epochs < 2 ||
+                         ctx->used + volume_bytes(vol->store, cells, vol->grid.n_epochs, 1, &stride) > ctx->budget))
+                continue;
+            for (const auto &ly : layouts) {
+                if ((rc = relayout_volume(*ctx, *vol, vid, ly[0], ly[1], pair))) return rc;
+                float ms = 0.f;
+                if ((rc = time_config(*ctx, *vol, hv, *spec, best, st, 3, ms))) return rc;
+                report(best, ms, ly[0], ly[1] + 10 * pair);
+                ++tried;
+                if (ms < best_ms) {
+                    best_ms = ms;
+                    bestB = ly[0];
+                    bestS = ly[1];
+                    bestP = pair;
+                }
             }
         }
-        if ((rc = relayout_volume(*ctx, *vol, vid, bestB, bestS))) return rc;
+        if ((rc = relayout_volume(*ctx, *vol, vid, bestB, bestS, bestP))) return rc;
     }
     TuneEntry e;
     e.cfg = best;

@@ -160,17 +160,25 @@ def test_batch_equals_single_bitwise(ctx):
     ctx.unload(vol)
 
 
-@pytest.mark.parametrize("brick,super_brick", [(1, 1), (4, 1), (4, 4), (8, 2), (2, 2)])
-def test_layouts_bitwise_identical(ctx, brick, super_brick):
+@pytest.mark.parametrize("brick,super_brick,paired", [(1, 1, 0), (4, 1, 0), (4, 4, 0), (8, 2, 0), (2, 2, 0),
+                                                     (8, 4, 1), (4, 2, 1), (1, 1, 1)])
+@pytest.mark.parametrize("store", ["f32", "bf16"])
+def test_layouts_bitwise_identical(ctx, brick, super_brick, paired, store):
+    """Every layout, paired snapshots included, gives the same image; the
+    windows of the views reach both ends of the stored snapshots."""
     grid, j, beta = random_grid(60, n=(19, 26, 33), M=4)
-    ref_vol = ctx.load_snapshots(grid, j, beta)
-    vol = ctx.load_snapshots(grid, j, beta, brick=brick, super_brick=super_brick)
-    v = gen.view_from_angles(grid, 37.0, 120.0, size=48, c=1.5, t_obs=3.0)
-    a = render_cpu(ctx, ref_vol, v)
-    b = render_cpu(ctx, vol, v)
-    assert np.array_equal(a, b)
+    ref_vol = ctx.load_snapshots(grid, j, beta, store=store)
+    vol = ctx.load_snapshots(grid, j, beta, store=store, brick=brick, super_brick=super_brick, paired=paired)
+    for t_obs in (-3.0, 3.0, 9.0):
+        v = gen.view_from_angles(grid, 37.0, 120.0, size=48, c=1.5, t_obs=t_obs)
+        a = render_cpu(ctx, ref_vol, v)
+        b = render_cpu(ctx, vol, v)
+        assert np.array_equal(a, b)
     info = ctx.volume_info(vol)
-    assert (info["brick"], info["super_brick"]) == (brick, super_brick)
+    assert (info["brick"], info["super_brick"], info["paired"]) == (brick, super_brick, paired)
+    # re-layout in place, in and out of the paired form
+    ctx.relayout(vol, 8, 2, not paired)
+    assert np.array_equal(render_cpu(ctx, vol, v), a)
     ctx.unload(vol)
     ctx.unload(ref_vol)
 
@@ -322,7 +330,7 @@ def test_tune_and_relayout_keep_results(ctx):
     after = ctx.render_batch(vol, views)
     torch.cuda.synchronize()
     assert np.array_equal(after.cpu().numpy(), before)
-    ctx.relayout(vol, 4, 2)
+    ctx.relayout(vol, 4, 2, True)
     again = ctx.render_batch(vol, views)
     torch.cuda.synchronize()
     assert np.array_equal(again.cpu().numpy(), before)
