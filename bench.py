@@ -179,8 +179,9 @@ def run_gpu(args, rank: int, world: int):
     n_views = len(views)
     ctx = Context(dev)
     t_load = time.perf_counter()
-    brick, sbrick = (int(x) for x in args.layout.split(",")) if args.layout else (0, 0)
-    vol = ctx.load_snapshots(wl["grid"], wl["j"], wl["beta"], store=wl["store"], brick=brick, super_brick=sbrick)
+    brick, sbrick, paired = ([int(x) for x in args.layout.split(",")] + [0])[:3] if args.layout else (0, 0, 0)
+    vol = ctx.load_snapshots(wl["grid"], wl["j"], wl["beta"], store=wl["store"], brick=brick, super_brick=sbrick,
+                             paired=bool(paired))
     torch.cuda.synchronize()
     t_load = time.perf_counter() - t_load
     info = ctx.volume_info(vol)
@@ -199,7 +200,7 @@ def run_gpu(args, rank: int, world: int):
         tuned = dict(launch)
     elif not args.no_tune:
         # autotune the launch (and, with --tune-layout, the volume layout) before timing
-        tuned = ctx.tune(vol, views, launch=True, layout=args.tune_layout, stream=stream)
+        tuned = ctx.tune(vol, views, launch=True, layout=not args.no_tune_layout, stream=stream)
         info = ctx.volume_info(vol)
 
     # cell-samples of one step (counted once, outside the timed region)
@@ -275,7 +276,8 @@ def run_gpu(args, rank: int, world: int):
                    "cell_samples_per_step": samples_per_step,
                    "volume_bytes": info["bytes"], "l2": "inputs larger than L2 (resident volume %.1f GB)"
                    % (info["bytes"] / 1e9), "parallelism": "replicas" if world > 1 else "single GPU",
-                   "layout": f"brick {info['brick']}, super-brick {info['super_brick']}",
+                   "layout": f"brick {info['brick']}, super-brick {info['super_brick']}"
+                             + (", paired snapshots" if info.get("paired") else ""),
                    "launch": ({k: tuned[k] for k in ("packet", "cta_warps", "depth", "persistent", "regcap")}
                               if tuned else "default")},
         "images_per_s": round(world * n_views / (ms_per_step * 1e-3), 2),
@@ -471,9 +473,10 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="oracle work for the cpu_baseline key")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="skip the launch autotuner (default configuration)")
-    ap.add_argument("--tune-layout", action="store_true", help="also autotune the volume's brick layout")
+    ap.add_argument("--tune-layout", action="store_true", help="(default) also autotune the volume's layout")
+    ap.add_argument("--no-tune-layout", action="store_true", help="keep the default brick layout")
     ap.add_argument("--launch", default="", help="fixed launch instead of tuning: packet_w,packet_h,warps,depth,regcap")
-    ap.add_argument("--layout", default="", help="fixed volume layout: brick,super_brick")
+    ap.add_argument("--layout", default="", help="fixed volume layout: brick,super_brick[,paired]")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
