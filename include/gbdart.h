@@ -108,7 +108,8 @@ typedef struct {
  *  vel : [M][n_z][n_y][n_x][3]  C order, components (x, y, z)
  * Both are read during the call only; the caller keeps ownership.  When
  * on_device is nonzero both are device pointers on the context's device,
- * otherwise host pointers.  j' < 0, non-finite values or |beta| >= 1 reject
+ * otherwise host pointers; device inputs are read after all work already
+ * launched on the device has finished (the call waits for it).  j' < 0, non-finite values or |beta| >= 1 reject
  * the whole load with GBD_ERR_INVALID. */
 typedef struct {
     const void *j;

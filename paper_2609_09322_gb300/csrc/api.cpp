@@ -611,6 +611,12 @@ int gbd_load_snapshots(gbd_ctx *ctx, const gbd_grid *grid, const gbd_fields *f, 
     e = cudaMalloc(reinterpret_cast<void **>(&vol->axis_off), tab_bytes);
     if (e != cudaSuccess) { cleanup(); return cuda_fail(e, "layout table allocation"); }
     cudaStream_t st = ctx->load_stream;
+    if (f->on_device) {
+        // Device inputs may still be being written by work on any stream of
+        // the caller (the call takes no stream): wait for the whole device.
+        e = cudaDeviceSynchronize();
+        if (e != cudaSuccess) { cleanup(); return cuda_fail(e, "wait for device inputs"); }
+    }
     e = cudaMemcpyAsync(vol->axis_off, tab.data(), tab_bytes, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(vol->rec, 0, bytes, st);
     if (e != cudaSuccess) { cleanup(); return cuda_fail(e, "volume init"); }

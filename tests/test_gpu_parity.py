@@ -336,3 +336,22 @@ def test_tune_and_relayout_keep_results(ctx):
     assert np.array_equal(again.cpu().numpy(), before)
     assert_parity(before[2], oracle.render(grid, j, beta, views[2]), what="tuned")
     ctx.unload(vol)
+
+
+def test_device_inputs_written_by_pending_work(ctx):
+    """Fields still being produced by queued GPU work on another stream are
+    read only after that work finishes."""
+    grid, j, beta = random_grid(91, n=(48, 40, 44), M=3)
+    side = torch.cuda.Stream()
+    with torch.cuda.stream(side):
+        jd = torch.zeros(j.shape, dtype=torch.float32, device="cuda:0")
+        bd = torch.zeros(beta.shape, dtype=torch.float32, device="cuda:0")
+        torch.cuda._sleep(50_000_000)   # keep the stream busy before the writes land
+        jd.copy_(torch.from_numpy(j).pin_memory(), non_blocking=True)
+        bd.copy_(torch.from_numpy(beta).pin_memory(), non_blocking=True)
+    vol = ctx.load_snapshots(grid, jd, bd)
+    ref_vol = ctx.load_snapshots(grid, j, beta)
+    v = gen.view_from_angles(grid, 33.0, 21.0, size=32, c=1.0, t_obs=2.0)
+    assert np.array_equal(render_cpu(ctx, vol, v), render_cpu(ctx, ref_vol, v))
+    ctx.unload(vol)
+    ctx.unload(ref_vol)
