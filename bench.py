@@ -175,6 +175,9 @@ def run_gpu(args, rank: int, world: int):
     dev = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(dev)
     wl = make_workload(args.workload, args.scale, device=f"cuda:{dev}")
+    if args.store:
+        wl["store"] = args.store
+        wl["desc"] += f"; stored as {'bf16 j + fp16 u' if args.store == 'bf16' else 'fp32'}"
     views = wl["views"]
     n_views = len(views)
     ctx = Context(dev)
@@ -198,7 +201,7 @@ def run_gpu(args, rank: int, world: int):
         pw, ph, warps, depth, regcap = (int(x) for x in args.launch.split(","))
         launch = {"packet": (pw, ph), "cta_warps": warps, "depth": depth, "persistent": 1, "regcap": regcap}
         tuned = dict(launch)
-    elif not args.no_tune:
+    elif not args.no_tune and not args.per_image:
         # autotune the launch (and, with --tune-layout, the volume layout) before timing
         tuned = ctx.tune(vol, views, launch=True, layout=not args.no_tune_layout, stream=stream)
         info = ctx.volume_info(vol)
@@ -211,8 +214,14 @@ def run_gpu(args, rank: int, world: int):
     del cnt
     out = torch.empty((n_views, views[0].height, views[0].width), dtype=torch.float32, device=f"cuda:{dev}")
 
-    def step():
-        ctx.render_batch(vol, views, out=out, launch=launch, stream=stream)
+    if args.per_image:
+        # the plain per-image march: one render call per view, no batching
+        def step():
+            for k, v in enumerate(views):
+                ctx.render(vol, v, out=out[k], launch=launch, stream=stream)
+    else:
+        def step():
+            ctx.render_batch(vol, views, out=out, launch=launch, stream=stream)
 
     for _ in range(args.warmup):
         step()
@@ -243,7 +252,7 @@ def run_gpu(args, rank: int, world: int):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         total_ms = float(t.item())
     ms_per_step = total_ms / args.steps
-    launches = args.steps * 1  # one march kernel per graph replay
+    launches = args.steps * (n_views if args.per_image else 1)  # march kernels in the timed region
 
     # end to end through the public API with host buffers
     host = torch.empty((n_views, views[0].height, views[0].width), dtype=torch.float32, pin_memory=True)
@@ -272,7 +281,8 @@ def run_gpu(args, rank: int, world: int):
         "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32" if wl["store"] == "f32" else "bf16/f16 storage, f32 math",
         "data": "synthetic (seeded generators in gen/)",
-        "config": {"workload": wl["desc"], "images_per_step": n_views,
+        "config": {"workload": wl["desc"] + ("; plain per-image renders" if args.per_image else ""),
+                   "images_per_step": n_views,
                    "cell_samples_per_step": samples_per_step,
                    "volume_bytes": info["bytes"], "l2": "inputs larger than L2 (resident volume %.1f GB)"
                    % (info["bytes"] / 1e9), "parallelism": "replicas" if world > 1 else "single GPU",
@@ -473,6 +483,9 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="oracle work for the cpu_baseline key")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="skip the launch autotuner (default configuration)")
+    ap.add_argument("--store", default="", choices=["", "f32", "bf16"], help="override the workload's storage")
+    ap.add_argument("--per-image", action="store_true",
+                    help="plain per-image march: one render call per view, default layout, no tuning")
     ap.add_argument("--tune-layout", action="store_true", help="(default) also autotune the volume's layout")
     ap.add_argument("--no-tune-layout", action="store_true", help="keep the default brick layout")
     ap.add_argument("--launch", default="", help="fixed launch instead of tuning: packet_w,packet_h,warps,depth,regcap")

@@ -123,6 +123,8 @@ typedef struct {
                             each cell side by side (M + 1 blocks), so a cell
                             sample under lookback is one contiguous load;
                             costs about 2 (M + 1) / M times the memory      */
+    int32_t morton_cells;/* 1: cells inside a brick in Morton order instead
+                            of x fastest                                    */
 } gbd_fields;
 
 /* One observation (Secs. 2.1-2.2, 2.5). */
@@ -166,7 +168,7 @@ typedef struct {
 typedef struct {
     gbd_grid grid;
     int32_t store;
-    int32_t brick, super_brick, paired;
+    int32_t brick, super_brick, paired, morton_cells;
     uint64_t bytes;          /* device bytes held by the packed volume       */
     uint64_t record_bytes;   /* 16 (F32) or 8 (BF16_F16U)                    */
 } gbd_volume_desc;
@@ -322,6 +324,8 @@ typedef struct {
     gbd_launch launch;       /* best launch configuration found            */
     int32_t brick;           /* layout of the volume after tuning          */
     int32_t super_brick;
+    int32_t paired;
+    int32_t morton_cells;
     float ms;                /* median time of the best candidate          */
     int32_t candidates;      /* configurations timed                       */
 } gbd_tune_result;
@@ -340,9 +344,11 @@ int gbd_tune(gbd_ctx *ctx, gbd_volume vol, const gbd_view *views, int32_t n, con
              uint32_t what, void *stream, gbd_tune_result *out);
 
 /* Re-packs a volume into another layout on the device (brick 1, 2, 4 or 8;
- * super_brick 1, 2 or 4; paired 0 or 1), keeping its handle.  Waits for the
- * device.  Needs room for both copies within the budget while it runs. */
-int gbd_relayout(gbd_ctx *ctx, gbd_volume vol, int32_t brick, int32_t super_brick, int32_t paired);
+ * super_brick 1, 2 or 4; paired 0 or 1; morton_cells 0 or 1), keeping its
+ * handle.  Waits for the device.  Needs room for both copies within the
+ * budget while it runs. */
+int gbd_relayout(gbd_ctx *ctx, gbd_volume vol, int32_t brick, int32_t super_brick, int32_t paired,
+                 int32_t morton_cells);
 
 /* Bounds checking.  In the library built with GBD_CHECKED every gather tests
  * its cell and epoch index against the volume; a violation skips the load and

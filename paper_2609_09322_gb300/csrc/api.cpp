@@ -76,7 +76,7 @@ static uint32_t spread3(uint32_t v)
     return r;
 }
 
-bool build_layout(const int n[3], int B, int S, std::vector<int32_t> &tab, long long &epoch_stride)
+bool build_layout(const int n[3], int B, int S, std::vector<int32_t> &tab, long long &epoch_stride, int morton_cells)
 {
     const long long E = static_cast<long long>(B) * S;
     long long P[3], NS[3];
@@ -97,7 +97,11 @@ bool build_layout(const int n[3], int B, int S, std::vector<int32_t> &tab, long 
             const long long sup = i / E;
             const uint32_t bin = static_cast<uint32_t>((i / B) % S);
             const long long morton = static_cast<long long>(spread3(bin)) << a;
-            tab[w++] = static_cast<int32_t>(sup * super_stride[a] + morton * B3 + (i % B) * cell_stride[a]);
+            // cells inside a brick: x fastest, or Morton order (bits of the
+            // three local coordinates interleaved, again one term per axis)
+            const long long local = morton_cells ? static_cast<long long>(spread3(static_cast<uint32_t>(i % B))) << a
+                                                 : (i % B) * cell_stride[a];
+            tab[w++] = static_cast<int32_t>(sup * super_stride[a] + morton * B3 + local);
         }
     }
     return true;
@@ -591,7 +595,8 @@ int gbd_load_snapshots(gbd_ctx *ctx, const gbd_grid *grid, const gbd_fields *f, 
     vol->paired = f->paired ? 1 : 0;
     std::vector<int32_t> tab;
     long long cells = 0;
-    if (!build_layout(g.n, B, S, tab, cells) || (vol->paired && 2 * cells >= (1LL << 31)))
+    vol->morton_cells = f->morton_cells ? 1 : 0;
+    if (!build_layout(g.n, B, S, tab, cells, vol->morton_cells) || (vol->paired && 2 * cells >= (1LL << 31)))
         return fail(GBD_ERR_INVALID, "grid too large: one epoch exceeds 2^31 records");
     const size_t rec_bytes = f->store == GBD_STORE_F32 ? 16 : 8;
     const size_t bytes = volume_bytes(f->store, cells, g.n_epochs, vol->paired, &vol->epoch_stride);
@@ -705,6 +710,7 @@ int gbd_volume_info(gbd_ctx *ctx, gbd_volume vid, gbd_volume_desc *out)
     out->brick = v->brick;
     out->super_brick = v->super_brick;
     out->paired = v->paired;
+    out->morton_cells = v->morton_cells;
     out->bytes = v->bytes;
     out->record_bytes = v->store == GBD_STORE_F32 ? 16 : 8;
     return GBD_OK;

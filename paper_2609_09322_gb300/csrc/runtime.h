@@ -21,6 +21,7 @@ struct Volume {
     int store = GBD_STORE_F32;
     int brick = 8, super_brick = 4;
     int paired = 0;                  // blocks of side-by-side snapshot pairs
+    int morton_cells = 0;            // Morton order of the cells inside a brick
     void *rec = nullptr;             // records, block after block
     int32_t *axis_off = nullptr;     // per-axis offset tables (n_x + n_y + n_z)
     long long epoch_stride = 0;      // records per block (epoch, or epoch pair)
@@ -97,7 +98,7 @@ LaunchCfg resolve_launch(const gbd_launch *l);
 int check_launch(const LaunchCfg &c);
 void fill_args(MarchArgs &a, const Volume &vol, const ViewDev *d_views, int n, const gbd_image_spec &s,
                float *out, uint32_t *samples, int *queue, const LaunchCfg &cfg, int *err_word);
-bool build_layout(const int n[3], int B, int S, std::vector<int32_t> &tab, long long &epoch_stride);
+bool build_layout(const int n[3], int B, int S, std::vector<int32_t> &tab, long long &epoch_stride, int morton_cells);
 void destroy_graph_cache(GraphCache *g);
 
 void drop_graphs_for(Ctx &ctx, gbd_volume vol);
@@ -108,7 +109,7 @@ int render_direct(Ctx &ctx, const Volume &vol, const std::vector<ViewDev> &hv, c
 TuneKey tune_key(const Volume &vol, int width, int height, int n_views, uint32_t flags);
 bool lookup_tuned(Ctx &ctx, const TuneKey &k, LaunchCfg &cfg);
 void load_tune_file(Ctx &ctx);
-int relayout_volume(Ctx &ctx, Volume &vol, gbd_volume vid, int B, int S, int paired);
+int relayout_volume(Ctx &ctx, Volume &vol, gbd_volume vid, int B, int S, int paired, int morton_cells);
 size_t volume_bytes(int store, long long cells_per_epoch, int M, int paired, long long *stride);
 
 // Serving (serve.cpp).

@@ -103,13 +103,15 @@ int time_config(Ctx &ctx, const Volume &vol, const std::vector<ViewDev> &hv, con
 // Re-packs a volume into another brick / super-brick layout on the device.
 // The handle keeps its identity; cached graphs of the volume are dropped
 // because their kernel parameters point at the old records.
-int relayout_volume(Ctx &ctx, Volume &vol, gbd_volume vid, int B, int S, int paired)
+int relayout_volume(Ctx &ctx, Volume &vol, gbd_volume vid, int B, int S, int paired, int morton_cells)
 {
     paired = paired ? 1 : 0;
-    if (B == vol.brick && S == vol.super_brick && paired == vol.paired) return GBD_OK;
+    morton_cells = morton_cells ? 1 : 0;
+    if (B == vol.brick && S == vol.super_brick && paired == vol.paired && morton_cells == vol.morton_cells)
+        return GBD_OK;
     std::vector<int32_t> tab;
     long long cells = 0, stride = 0;
-    if (!build_layout(vol.grid.n, B, S, tab, cells) || (paired && 2 * cells >= (1LL << 31)))
+    if (!build_layout(vol.grid.n, B, S, tab, cells, morton_cells) || (paired && 2 * cells >= (1LL << 31)))
         return fail(GBD_ERR_INVALID, "layout too large");
     const size_t rec_bytes = vol.store == GBD_STORE_F32 ? 16 : 8;
     const size_t bytes = volume_bytes(vol.store, cells, vol.grid.n_epochs, paired, &stride);
@@ -162,6 +164,7 @@ int relayout_volume(Ctx &ctx, Volume &vol, gbd_volume vid, int B, int S, int pai
     vol.brick = B;
     vol.super_brick = S;
     vol.paired = paired;
+    vol.morton_cells = morton_cells;
     vol.bytes = bytes + tab_bytes;
     ctx.used += vol.bytes;
     return GBD_OK;
@@ -203,7 +206,8 @@ using namespace gbd;
 
 extern "C" {
 
-int gbd_relayout(gbd_ctx *ctx, gbd_volume vid, int32_t brick, int32_t super_brick, int32_t paired)
+int gbd_relayout(gbd_ctx *ctx, gbd_volume vid, int32_t brick, int32_t super_brick, int32_t paired,
+                 int32_t morton_cells)
 {
     if (!ctx) return fail(GBD_ERR_INVALID, "ctx is NULL");
     if (brick != 1 && brick != 2 && brick != 4 && brick != 8) return fail(GBD_ERR_INVALID, "brick must be 1, 2, 4 or 8");
@@ -215,7 +219,7 @@ int gbd_relayout(gbd_ctx *ctx, gbd_volume vid, int32_t brick, int32_t super_bric
     if (v->pinned_by_requests.load() > 0) return fail(GBD_ERR_BUSY, "volume has queued requests");
     DeviceGuard guard(ctx->device);
     if (paired != 0 && paired != 1) return fail(GBD_ERR_INVALID, "paired must be 0 or 1");
-    return relayout_volume(*ctx, *v, vid, brick, super_brick, paired);
+    return relayout_volume(*ctx, *v, vid, brick, super_brick, paired, morton_cells);
 }
 
 int gbd_tune(gbd_ctx *ctx, gbd_volume vid, const gbd_view *views, int32_t n, const gbd_image_spec *spec,
@@ -278,31 +282,34 @@ int gbd_tune(gbd_ctx *ctx, gbd_volume vid, const gbd_view *views, int32_t n, con
         }
     }
     if (what & GBD_TUNE_LAYOUT) {
-        const int layouts[6][2] = {{8, 4}, {8, 2}, {8, 1}, {4, 4}, {4, 2}, {1, 1}};
-        int bestB = vol->brick, bestS = vol->super_brick, bestP = vol->paired;
+        // brick, super-brick, Morton cells
+        const int layouts[9][3] = {{8, 4, 0}, {8, 2, 0}, {8, 1, 0}, {4, 4, 0}, {4, 2, 0}, {1, 1, 0},
+                                   {8, 4, 1}, {4, 4, 1}, {4, 2, 1}};
+        int bestB = vol->brick, bestS = vol->super_brick, bestP = vol->paired, bestZ = vol->morton_cells;
         for (int pair = 0; pair < 2; ++pair) {
             // the paired form is tried when two copies of it fit the budget
             long long cells = 0, stride = 0;
             std::vector<int32_t> tab;
-            build_layout(vol->grid.n, 8, 4, tab, cells);
+            build_layout(vol->grid.n, 8, 4, tab, cells, 0);
             if (pair && (vol->grid.n_epochs < 2 ||
                          ctx->used + volume_bytes(vol->store, cells, vol->grid.n_epochs, 1, &stride) > ctx->budget))
                 continue;
             for (const auto &ly : layouts) {
-                if ((rc = relayout_volume(*ctx, *vol, vid, ly[0], ly[1], pair))) return rc;
+                if ((rc = relayout_volume(*ctx, *vol, vid, ly[0], ly[1], pair, ly[2]))) return rc;
                 float ms = 0.f;
                 if ((rc = time_config(*ctx, *vol, hv, *spec, best, st, 3, ms))) return rc;
-                report(best, ms, ly[0], ly[1] + 10 * pair);
+                report(best, ms, ly[0], ly[1] + 10 * pair + 100 * ly[2]);
                 ++tried;
                 if (ms < best_ms) {
                     best_ms = ms;
                     bestB = ly[0];
                     bestS = ly[1];
                     bestP = pair;
+                    bestZ = ly[2];
                 }
             }
         }
-        if ((rc = relayout_volume(*ctx, *vol, vid, bestB, bestS, bestP))) return rc;
+        if ((rc = relayout_volume(*ctx, *vol, vid, bestB, bestS, bestP, bestZ))) return rc;
     }
     TuneEntry e;
     e.cfg = best;
@@ -320,6 +327,8 @@ int gbd_tune(gbd_ctx *ctx, gbd_volume vid, const gbd_view *views, int32_t n, con
     out->launch.regcap = best.regcap;
     out->brick = vol->brick;
     out->super_brick = vol->super_brick;
+    out->paired = vol->paired;
+    out->morton_cells = vol->morton_cells;
     out->ms = best_ms;
     out->candidates = tried;
     return GBD_OK;

@@ -40,7 +40,7 @@ class Grid(ctypes.Structure):
 class Fields(ctypes.Structure):
     _fields_ = [("j", ctypes.c_void_p), ("vel", ctypes.c_void_p), ("dtype_in", ctypes.c_int32),
                 ("store", ctypes.c_int32), ("on_device", ctypes.c_int32), ("brick", ctypes.c_int32),
-                ("super_brick", ctypes.c_int32), ("paired", ctypes.c_int32)]
+                ("super_brick", ctypes.c_int32), ("paired", ctypes.c_int32), ("morton_cells", ctypes.c_int32)]
 
 
 class CView(ctypes.Structure):
@@ -62,7 +62,8 @@ class Launch(ctypes.Structure):
 
 class TuneResult(ctypes.Structure):
     _fields_ = [("launch", Launch), ("brick", ctypes.c_int32), ("super_brick", ctypes.c_int32),
-                ("ms", ctypes.c_float), ("candidates", ctypes.c_int32)]
+                ("paired", ctypes.c_int32), ("morton_cells", ctypes.c_int32), ("ms", ctypes.c_float),
+                ("candidates", ctypes.c_int32)]
 
 
 TUNE_LAUNCH, TUNE_LAYOUT = 1, 2
@@ -92,7 +93,8 @@ class ServeSummary(ctypes.Structure):
 
 class VolumeDesc(ctypes.Structure):
     _fields_ = [("grid", Grid), ("store", ctypes.c_int32), ("brick", ctypes.c_int32),
-                ("super_brick", ctypes.c_int32), ("paired", ctypes.c_int32), ("bytes", ctypes.c_uint64),
+                ("super_brick", ctypes.c_int32), ("paired", ctypes.c_int32), ("morton_cells", ctypes.c_int32),
+                ("bytes", ctypes.c_uint64),
                 ("record_bytes", ctypes.c_uint64)]
 
 
@@ -125,8 +127,8 @@ _SIGNATURES = {
     "gbd_tune": ([ctypes.c_void_p, ctypes.c_uint64, ctypes.POINTER(CView), ctypes.c_int32,
                   ctypes.POINTER(ImageSpec), ctypes.c_uint32, ctypes.c_void_p, ctypes.POINTER(TuneResult)],
                  ctypes.c_int),
-    "gbd_relayout": ([ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32],
-                     ctypes.c_int),
+    "gbd_relayout": ([ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                      ctypes.c_int32], ctypes.c_int),
     "gbd_render_batch": ([ctypes.c_void_p, ctypes.c_uint64, ctypes.POINTER(CView), ctypes.c_int32,
                           ctypes.POINTER(ImageSpec), ctypes.POINTER(Launch), ctypes.c_void_p], ctypes.c_int),
 }
@@ -224,7 +226,7 @@ class Context:
 
     # -- volumes
     def load_snapshots(self, grid, j, beta, *, store="f32", brick: int = 0, super_brick: int = 0,
-                       paired: bool = False) -> int:
+                       paired: bool = False, morton_cells: bool = False) -> int:
         """Pack snapshots j[M][nz][ny][nx] and beta[M][nz][ny][nx][3] (numpy
         arrays or torch tensors, float64 or float32) into a resident volume."""
         import torch
@@ -266,6 +268,7 @@ class Context:
         f.brick = int(brick)
         f.super_brick = int(super_brick)
         f.paired = int(bool(paired))
+        f.morton_cells = int(bool(morton_cells))
         vid = ctypes.c_uint64()
         rc = self.lib.gbd_load_snapshots(self.handle, ctypes.byref(g), ctypes.byref(f), ctypes.byref(vid))
         del keep
@@ -279,7 +282,8 @@ class Context:
         d = VolumeDesc()
         _check(self.lib, self.lib.gbd_volume_info(self.handle, int(vol), ctypes.byref(d)))
         return dict(n=tuple(d.grid.n), n_epochs=d.grid.n_epochs, store=d.store, brick=d.brick,
-                    super_brick=d.super_brick, paired=d.paired, bytes=int(d.bytes), record_bytes=int(d.record_bytes))
+                    super_brick=d.super_brick, paired=d.paired, morton_cells=d.morton_cells, bytes=int(d.bytes),
+                    record_bytes=int(d.record_bytes))
 
     # -- rendering
     def _spec(self, view, out_ptr, samples_ptr, on_host=False) -> ImageSpec:
@@ -371,11 +375,11 @@ class Context:
         lw = res.launch
         return dict(packet=(lw.packet_w, lw.packet_h), cta_warps=lw.cta_warps, depth=lw.depth,
                     persistent=lw.persistent, regcap=lw.regcap, brick=res.brick, super_brick=res.super_brick,
-                    ms=res.ms, candidates=res.candidates)
+                    paired=res.paired, morton_cells=res.morton_cells, ms=res.ms, candidates=res.candidates)
 
-    def relayout(self, vol: int, brick: int, super_brick: int, paired: bool = False):
+    def relayout(self, vol: int, brick: int, super_brick: int, paired: bool = False, morton_cells: bool = False):
         _check(self.lib, self.lib.gbd_relayout(self.handle, int(vol), int(brick), int(super_brick),
-                                               int(bool(paired))))
+                                               int(bool(paired)), int(bool(morton_cells))))
 
     def bounds_violations(self) -> int:
         """Device bounds-check word of the checked library (waits for the

@@ -160,24 +160,27 @@ def test_batch_equals_single_bitwise(ctx):
     ctx.unload(vol)
 
 
-@pytest.mark.parametrize("brick,super_brick,paired", [(1, 1, 0), (4, 1, 0), (4, 4, 0), (8, 2, 0), (2, 2, 0),
-                                                     (8, 4, 1), (4, 2, 1), (1, 1, 1)])
+@pytest.mark.parametrize("brick,super_brick,paired,morton", [(1, 1, 0, 0), (4, 1, 0, 0), (4, 4, 0, 0), (8, 2, 0, 0),
+                                                            (2, 2, 0, 0), (8, 4, 1, 0), (4, 2, 1, 0), (1, 1, 1, 0),
+                                                            (8, 4, 0, 1), (4, 2, 1, 1)])
 @pytest.mark.parametrize("store", ["f32", "bf16"])
-def test_layouts_bitwise_identical(ctx, brick, super_brick, paired, store):
+def test_layouts_bitwise_identical(ctx, brick, super_brick, paired, morton, store):
     """Every layout, paired snapshots included, gives the same image; the
     windows of the views reach both ends of the stored snapshots."""
     grid, j, beta = random_grid(60, n=(19, 26, 33), M=4)
     ref_vol = ctx.load_snapshots(grid, j, beta, store=store)
-    vol = ctx.load_snapshots(grid, j, beta, store=store, brick=brick, super_brick=super_brick, paired=paired)
+    vol = ctx.load_snapshots(grid, j, beta, store=store, brick=brick, super_brick=super_brick, paired=paired,
+                             morton_cells=morton)
     for t_obs in (-3.0, 3.0, 9.0):
         v = gen.view_from_angles(grid, 37.0, 120.0, size=48, c=1.5, t_obs=t_obs)
         a = render_cpu(ctx, ref_vol, v)
         b = render_cpu(ctx, vol, v)
         assert np.array_equal(a, b)
     info = ctx.volume_info(vol)
-    assert (info["brick"], info["super_brick"], info["paired"]) == (brick, super_brick, paired)
-    # re-layout in place, in and out of the paired form
-    ctx.relayout(vol, 8, 2, not paired)
+    assert (info["brick"], info["super_brick"], info["paired"], info["morton_cells"]) == \
+        (brick, super_brick, paired, morton)
+    # re-layout in place, in and out of the paired form and the Morton cells
+    ctx.relayout(vol, 8, 2, not paired, not morton)
     assert np.array_equal(render_cpu(ctx, vol, v), a)
     ctx.unload(vol)
     ctx.unload(ref_vol)
