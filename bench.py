@@ -252,7 +252,9 @@ def run_gpu(args, rank: int, world: int):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         total_ms = float(t.item())
     ms_per_step = total_ms / args.steps
-    launches = args.steps * (n_views if args.per_image else 1)  # march kernels in the timed region
+    step()  # one more, untimed, to read how many march kernels a step launches
+    stream.synchronize()
+    launches = args.steps * (n_views if args.per_image else ctx.last_launch_count())
 
     # end to end through the public API with host buffers
     host = torch.empty((n_views, views[0].height, views[0].width), dtype=torch.float32, pin_memory=True)

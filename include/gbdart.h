@@ -160,7 +160,8 @@ typedef struct {
     int32_t packet_w, packet_h;  /* pixels of one warp packet: 8x4, 4x8, 16x2, 32x1 */
     int32_t cta_warps;           /* warps per CTA: 1, 2, 4 or 8                     */
     int32_t depth;               /* cells gathered ahead per lane: 1, 2 or 4       */
-    int32_t persistent;          /* 1 = persistent grid over a tile queue           */
+    int32_t persistent;          /* 1 = CTAs loop over their view's tile counter;
+                                    0 = one packet per warp, one launch wave    */
     int32_t regcap;              /* 1 = kernel built for at most 80 registers/thread */
 } gbd_launch;
 
@@ -206,11 +207,13 @@ int gbd_volume_info(gbd_ctx *ctx, gbd_volume vol, gbd_volume_desc *out);
 int gbd_render(gbd_ctx *ctx, gbd_volume vol, const gbd_view *view, const gbd_image_spec *spec,
                const gbd_launch *launch, void *stream);
 
-/* Renders n views of the same image geometry in one persistent launch over a
- * shared tile queue; view k goes to spec->out + k * width * height (and the
- * sample counts likewise).  The view table and the queue counter live in a
- * context-owned device buffer; the launch is captured once into a CUDA graph
- * per (volume, n, geometry, destination, launch) and replayed afterwards.
+/* Renders n views of the same image geometry; view k goes to spec->out +
+ * k * width * height (and the sample counts likewise).  Views travel in the
+ * kernel launch parameters, up to 128 per launch (larger batches are several
+ * launches); the per-view tile counters live in a context-owned device
+ * buffer.  The launches are built once into a CUDA graph per (volume, n,
+ * geometry, destination, launch) and replayed afterwards, with new views
+ * written into the graph's kernel parameters.
  * Concurrent batch calls on one context are serialised on the context's lock,
  * and the GPU work of consecutive calls is ordered on their streams. */
 int gbd_render_batch(gbd_ctx *ctx, gbd_volume vol, const gbd_view *views, int32_t n,
@@ -221,10 +224,10 @@ int gbd_render_batch(gbd_ctx *ctx, gbd_volume vol, const gbd_view *views, int32_
  * memory while they render -- applications that hand the whole device to
  * their own allocator or memory pool up front, and latency-critical loops
  * where cudaMalloc / cudaFree (which may synchronise the device) are not
- * acceptable.  It renders like gbd_render_batch, but keeps the view table and
- * the tile counter of the persistent launch in one fixed-size device array of
- * the library (about 208 KB, held by every GPU that loads the library until
- * the process exits) instead of allocating them, and uses no CUDA graph.
+ * acceptable.  It renders like gbd_render_batch, but keeps the per-view tile
+ * counters of the persistent launch in one fixed-size device array of the
+ * library (4 KB, held by every GPU that loads the library until the process
+ * exits) instead of allocating them, and uses no CUDA graph.
  * Limits and behaviour:
  *  - at most GBD_NOALLOC_MAX_VIEWS views per call, otherwise GBD_ERR_INVALID;
  *  - spec->out (and spec->samples, if set) must be device memory;
@@ -233,7 +236,7 @@ int gbd_render_batch(gbd_ctx *ctx, gbd_volume vol, const gbd_view *views, int32_
  *    device (cudaGetSymbolAddress); make that first call before any stream
  *    capture;
  *  - every call shares the one array, which keeps the last call's contents
- *    (the tile counter is cleared by each call): calls whose GPU work overlaps,
+ *    (the tile counters are cleared by each call): calls whose GPU work overlaps,
  *    from any context or stream on the same device, race on it, so the caller
  *    orders them (for example on one stream). */
 #define GBD_NOALLOC_MAX_VIEWS 1024
@@ -250,7 +253,8 @@ int32_t gbd_last_launch_count(void);
  * thread of the context admits them into waves as request slots and device
  * memory free up (a request holds its library-side device bytes -- its image,
  * when the output is host memory -- from launch to completion) and runs each
- * wave as one persistent launch over all of its requests' pixel tiles.  Up to
+ * wave as launches over all of its requests' pixel tiles (up to 96 requests
+ * per launch, one CTA per warps-per-CTA tiles of a request).  Up to
  * max_waves waves are on the GPU at once on separate streams, so requests that
  * arrive while others run start as soon as the GPU has room.  Every pixel is
  * computed by the same per-ray code as gbd_render, so a request's image is the

@@ -104,6 +104,20 @@ bool build_layout(const int n[3], int B, int S, std::vector<int32_t> &tab, long 
             tab[w++] = static_cast<int32_t>(sup * super_stride[a] + morton * B3 + local);
         }
     }
+    // the march tables follow the pack tables in the same device array
+    tab.resize(w + static_cast<size_t>(march_table_entries(n)));
+    size_t src = 0;
+    for (int a = 0; a < 3; ++a) {
+        int32_t *fwd = tab.data() + w + march_table_base(n, a);
+        int32_t *rev = fwd + n[a] + 2;
+        for (int i = 0; i < n[a]; ++i) {
+            fwd[i] = tab[src + i];
+            rev[i] = tab[src + n[a] - 1 - i];
+        }
+        fwd[n[a]] = fwd[n[a] + 1] = kTabSentinel;
+        rev[n[a]] = rev[n[a] + 1] = kTabSentinel;
+        src += n[a];
+    }
     return true;
 }
 
@@ -169,12 +183,18 @@ int make_view(const Volume &vol, const gbd_view &v, int width, int height, doubl
         const double gu = hu * eu[i] / g.dx[i], gv = hv * ev[i] / g.dx[i];
         // every pixel position must stay within the fixed-point range
         reach = std::max(reach, std::fabs(g00) + std::fabs(gu) * width + std::fabs(gv) * height + g.n[i]);
-        out.g0[i] = std::llround(g00 * two40);
-        out.gu[i] = std::llround(gu * two40);
-        out.gv[i] = std::llround(gv * two40);
         // Components below 1e-9 count as parallel: such a ray moves less than
         // 1e-9 cells per unit length along that axis.
-        const double a = std::fabs(sh[i]) < 1e-9 ? 0.0 : sh[i] / g.dx[i];
+        const bool parallel = std::fabs(sh[i]) < 1e-9;
+        // An axis the ray runs down is mirrored, g' = n - g, exactly in fixed
+        // point, so that the march always steps up.
+        const bool mirror = !parallel && sh[i] < 0.0;
+        const long long n40 = static_cast<long long>(g.n[i]) << 40;
+        out.g0[i] = mirror ? n40 - std::llround(g00 * two40) : std::llround(g00 * two40);
+        out.gu[i] = mirror ? -std::llround(gu * two40) : std::llround(gu * two40);
+        out.gv[i] = mirror ? -std::llround(gv * two40) : std::llround(gv * two40);
+        if (mirror) out.flags |= kFlagMirror0 << i;
+        const double a = parallel ? 0.0 : std::fabs(sh[i]) / g.dx[i];
         out.a_hi[i] = static_cast<float>(a);
         out.a_lo[i] = static_cast<float>(a - static_cast<double>(out.a_hi[i]));
         out.inv_a[i] = a != 0.0 ? static_cast<float>(1.0 / a) : 0.0f;
@@ -199,7 +219,7 @@ int make_view(const Volume &vol, const gbd_view &v, int width, int height, doubl
     const float fbig = 3.0e38f;
     out.win_lo = win_lo <= -1e38 ? -fbig : (win_lo >= 1e38 ? fbig : static_cast<float>(win_lo - 1e-6 * (1.0 + std::fabs(win_lo))));
     out.win_hi = win_hi >= 1e38 ? fbig : (win_hi <= -1e38 ? -fbig : static_cast<float>(win_hi + 1e-6 * (1.0 + std::fabs(win_hi))));
-    out.flags = v.flags;
+    out.flags |= v.flags;
     out.expo = static_cast<float>(2.0 - v.alpha);
     out.prefactor = static_cast<float>(std::pow(v.nu_ratio, v.alpha));
     if (!(out.prefactor > 0.0f) || !std::isfinite(out.prefactor))
@@ -221,6 +241,7 @@ VolDev vol_dev(const Volume &v)
     std::memset(&d, 0, sizeof(d));
     d.rec = v.rec;
     d.axis_off = v.axis_off;
+    d.mtab = v.axis_off + (v.grid.n[0] + v.grid.n[1] + v.grid.n[2]);
     d.epoch_stride = v.epoch_stride;
     for (int i = 0; i < 3; ++i) d.n[i] = v.grid.n[i];
     d.M = v.grid.n_epochs;
@@ -262,54 +283,65 @@ int check_spec(const gbd_image_spec *s)
     return GBD_OK;
 }
 
-void fill_args(MarchArgs &a, const Volume &vol, const ViewDev *d_views, int n, const gbd_image_spec &s,
+int march_chunks(int n) { return (n + kViewsPerLaunch - 1) / kViewsPerLaunch; }
+
+// Launch arguments of chunk c of a batch of n views: views c K .. c K + K - 1
+// (K = kViewsPerLaunch), their images and their tile counters.
+void fill_args(MarchArgs &a, const Volume &vol, const ViewDev *hv, int n, int c, const gbd_image_spec &s,
                float *out, uint32_t *samples, int *queue, const LaunchCfg &cfg, int *err_word)
 {
     std::memset(&a, 0, sizeof(a));
+    const int first = c * kViewsPerLaunch;
+    const int cnt = std::min(kViewsPerLaunch, n - first);
+    const size_t img = static_cast<size_t>(first) * s.width * s.height;
     a.vol = vol_dev(vol);
-    a.views = d_views;
-    a.n_views = n;
+    a.n_views = cnt;
     a.width = s.width;
     a.height = s.height;
     a.packet_w = cfg.packet_w;
     a.packet_h = cfg.packet_h;
     a.tiles_x = (s.width + cfg.packet_w - 1) / cfg.packet_w;
     a.tiles_y = (s.height + cfg.packet_h - 1) / cfg.packet_h;
-    a.total_items = static_cast<long long>(n) * a.tiles_x * a.tiles_y;
-    a.out = out;
-    a.samples = samples;
-    a.queue = queue;
-    a.error_word = err_word;
     a.persistent = cfg.persistent;
+    a.out = out + img;
+    a.samples = samples ? samples + img : nullptr;
+    a.queue = queue + first;
+    a.error_word = err_word;
+    std::memcpy(a.views, hv + first, sizeof(ViewDev) * static_cast<size_t>(cnt));
 }
 
+// Bytes of the per-view tile counters of a batch, rounded up to 256.
+static size_t queue_bytes(int n) { return (static_cast<size_t>(n) * sizeof(int) + 255) / 256 * 256; }
+
 // Renders n views whose records are already set up on the host, without a
-// cached graph: stream-ordered scratch for the view table and queue counter.
+// cached graph: stream-ordered scratch for the tile counters (and the image
+// when it goes to host memory), one launch per kViewsPerLaunch views.
 int render_direct(Ctx &ctx, const Volume &vol, const std::vector<ViewDev> &hv, const gbd_image_spec &spec,
                   const LaunchCfg &cfg, cudaStream_t st)
 {
     const int n = static_cast<int>(hv.size());
-    const size_t vbytes = sizeof(ViewDev) * hv.size();
     const size_t pix = static_cast<size_t>(spec.width) * spec.height * n;
     char *scratch = nullptr;
-    const size_t img_off = (vbytes + 255) / 256 * 256 + 256;
+    const size_t img_off = queue_bytes(n);
     const size_t total = img_off + (spec.out_on_host ? pix * sizeof(float) : 0);
     cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&scratch), total, st);
     if (e != cudaSuccess) return cuda_fail(e, "render scratch");
-    ViewDev *d_views = reinterpret_cast<ViewDev *>(scratch);
-    int *queue = reinterpret_cast<int *>(scratch + img_off - 256);
+    int *queue = reinterpret_cast<int *>(scratch);
     float *dev_out = spec.out_on_host ? reinterpret_cast<float *>(scratch + img_off) : spec.out;
-    e = cudaMemcpyAsync(d_views, hv.data(), vbytes, cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(queue, 0, 256, st);
-    MarchArgs a;
-    fill_args(a, vol, d_views, n, spec, dev_out, spec.out_on_host ? nullptr : spec.samples, queue, cfg, ctx.err_word);
-    if (e == cudaSuccess) e = launch_march(a, cfg, ctx.num_sms, st);
+    e = cudaMemsetAsync(queue, 0, img_off, st);
+    const int chunks = march_chunks(n);
+    auto a = std::make_unique<MarchArgs>();
+    for (int c = 0; c < chunks && e == cudaSuccess; ++c) {
+        fill_args(*a, vol, hv.data(), n, c, spec, dev_out, spec.out_on_host ? nullptr : spec.samples, queue, cfg,
+                  ctx.err_word);
+        e = launch_march(*a, cfg, ctx.num_sms, st);
+    }
     if (e == cudaSuccess && spec.out_on_host)
         e = cudaMemcpyAsync(spec.out, dev_out, pix * sizeof(float), cudaMemcpyDeviceToHost, st);
     cudaError_t ef = cudaFreeAsync(scratch, st);
     if (e != cudaSuccess) return cuda_fail(e, "render launch");
     if (ef != cudaSuccess) return cuda_fail(ef, "render scratch free");
-    set_launch_count(1);
+    set_launch_count(chunks);
     return GBD_OK;
 }
 
@@ -327,17 +359,23 @@ struct GraphKey {
     }
 };
 
+// A batch graph: a memset of the tile counters, one kernel node per chunk of
+// views (independent, so they may run side by side), and, for host output,
+// the copy back.  New views of the same geometry update the kernel nodes'
+// parameters in place.
 struct GraphEntry {
+    cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
-    char *d_scratch = nullptr;  // view table + queue counter (+ image when out_on_host)
-    ViewDev *h_views = nullptr; // pinned staging of the view table
+    std::vector<cudaGraphNode_t> knodes;
+    std::vector<ViewDev> views;  // the views the kernel nodes hold
+    char *d_scratch = nullptr;   // tile counters (+ image when out_on_host)
     cudaEvent_t done = nullptr;
     bool launched = false;
     ~GraphEntry()
     {
         if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
         if (done) cudaEventDestroy(done);
-        if (h_views) cudaFreeHost(h_views);
         if (d_scratch) cudaFree(d_scratch);
     }
 };
@@ -368,45 +406,72 @@ void drop_graphs_for(Ctx &ctx, gbd_volume vol)
     }
 }
 
+// Kernel node parameters of chunk c of a graph's batch.
+static cudaError_t chunk_params(Ctx &ctx, const Volume &vol, const GraphKey &key, const gbd_image_spec &spec,
+                                const GraphEntry &g, const ViewDev *hv, int c, MarchArgs &a,
+                                cudaKernelNodeParams &kp, void **params)
+{
+    const size_t img_off = queue_bytes(key.n);
+    int *queue = reinterpret_cast<int *>(g.d_scratch);
+    float *dev_out = spec.out_on_host ? reinterpret_cast<float *>(g.d_scratch + img_off) : spec.out;
+    fill_args(a, vol, hv, key.n, c, spec, dev_out, spec.out_on_host ? nullptr : spec.samples, queue, key.cfg,
+              ctx.err_word);
+    KernelLaunch L;
+    cudaError_t e = plan_march(a, key.cfg, ctx.num_sms, L);
+    if (e != cudaSuccess) return e;
+    std::memset(&kp, 0, sizeof(kp));
+    kp.func = L.func;
+    kp.gridDim = L.grid;
+    kp.blockDim = L.block;
+    kp.sharedMemBytes = static_cast<unsigned>(L.smem);
+    params[0] = &a;
+    kp.kernelParams = params;
+    return cudaSuccess;
+}
+
 static int build_graph(Ctx &ctx, const Volume &vol, const GraphKey &key, const gbd_image_spec &spec,
-                       GraphEntry &g)
+                       const std::vector<ViewDev> &hv, GraphEntry &g)
 {
     const int n = key.n;
-    const size_t vbytes = sizeof(ViewDev) * n;
-    const size_t img_off = (vbytes + 255) / 256 * 256 + 256;
+    const size_t img_off = queue_bytes(n);
     const size_t pix = static_cast<size_t>(spec.width) * spec.height * n;
     const size_t total = img_off + (spec.out_on_host ? pix * sizeof(float) : 0);
     cudaError_t e = cudaMalloc(reinterpret_cast<void **>(&g.d_scratch), total);
     if (e != cudaSuccess) return cuda_fail(e, "batch scratch");
-    e = cudaMallocHost(reinterpret_cast<void **>(&g.h_views), vbytes);
-    if (e != cudaSuccess) return cuda_fail(e, "batch pinned staging");
     e = cudaEventCreateWithFlags(&g.done, cudaEventDisableTiming);
     if (e != cudaSuccess) return cuda_fail(e, "batch event");
-    ViewDev *d_views = reinterpret_cast<ViewDev *>(g.d_scratch);
-    int *queue = reinterpret_cast<int *>(g.d_scratch + img_off - 256);
-    float *dev_out = spec.out_on_host ? reinterpret_cast<float *>(g.d_scratch + img_off) : spec.out;
-
-    cudaStream_t cap = ctx.capture_stream;
-    e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
-    if (e != cudaSuccess) return cuda_fail(e, "begin capture");
-    cudaError_t e2 = cudaMemcpyAsync(d_views, g.h_views, vbytes, cudaMemcpyHostToDevice, cap);
-    if (e2 == cudaSuccess) e2 = cudaMemsetAsync(queue, 0, 256, cap);
-    MarchArgs a;
-    fill_args(a, vol, d_views, n, spec, dev_out, spec.out_on_host ? nullptr : spec.samples, queue, key.cfg,
-              ctx.err_word);
-    if (e2 == cudaSuccess) e2 = launch_march(a, key.cfg, ctx.num_sms, cap);
-    if (e2 == cudaSuccess && spec.out_on_host)
-        e2 = cudaMemcpyAsync(spec.out, dev_out, pix * sizeof(float), cudaMemcpyDeviceToHost, cap);
-    cudaGraph_t graph = nullptr;
-    e = cudaStreamEndCapture(cap, &graph);
-    if (e2 != cudaSuccess) {
-        if (graph) cudaGraphDestroy(graph);
-        return cuda_fail(e2, "capture batch");
+    e = cudaGraphCreate(&g.graph, 0);
+    if (e != cudaSuccess) return cuda_fail(e, "batch graph");
+    cudaMemsetParams mp;
+    std::memset(&mp, 0, sizeof(mp));
+    mp.dst = g.d_scratch;
+    mp.value = 0;
+    mp.elementSize = 4;
+    mp.width = img_off / 4;
+    mp.height = 1;
+    cudaGraphNode_t mnode = nullptr;
+    e = cudaGraphAddMemsetNode(&mnode, g.graph, nullptr, 0, &mp);
+    if (e != cudaSuccess) return cuda_fail(e, "batch graph memset node");
+    auto a = std::make_unique<MarchArgs>();
+    const int chunks = march_chunks(n);
+    for (int c = 0; c < chunks; ++c) {
+        cudaKernelNodeParams kp;
+        void *params[1];
+        e = chunk_params(ctx, vol, key, spec, g, hv.data(), c, *a, kp, params);
+        cudaGraphNode_t kn = nullptr;
+        if (e == cudaSuccess) e = cudaGraphAddKernelNode(&kn, g.graph, &mnode, 1, &kp);
+        if (e != cudaSuccess) return cuda_fail(e, "batch graph kernel node");
+        g.knodes.push_back(kn);
     }
-    if (e != cudaSuccess) return cuda_fail(e, "end capture");
-    e = cudaGraphInstantiate(&g.exec, graph, 0);
-    cudaGraphDestroy(graph);
+    if (spec.out_on_host) {
+        cudaGraphNode_t cn = nullptr;
+        e = cudaGraphAddMemcpyNode1D(&cn, g.graph, g.knodes.data(), g.knodes.size(), spec.out,
+                                     g.d_scratch + img_off, pix * sizeof(float), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_fail(e, "batch graph copy node");
+    }
+    e = cudaGraphInstantiate(&g.exec, g.graph, 0);
     if (e != cudaSuccess) return cuda_fail(e, "instantiate batch graph");
+    g.views = hv;
     return GBD_OK;
 }
 
@@ -438,28 +503,32 @@ int render_graph(Ctx &ctx, const Volume &vol, gbd_volume vid, const std::vector<
     const size_t vbytes = sizeof(ViewDev) * hv.size();
     if (!slot) {
         auto g = std::make_unique<GraphEntry>();
-        int rc = build_graph(ctx, vol, key, spec, *g);
+        int rc = build_graph(ctx, vol, key, spec, hv, *g);
         if (rc != GBD_OK) {
             gc.entries.erase(key);
             gc.last_use.erase(key);
             return rc;
         }
-        std::memcpy(g->h_views, hv.data(), vbytes);
         slot = std::move(g);
-    } else if (std::memcmp(slot->h_views, hv.data(), vbytes) != 0) {
-        // The previous replay may still be reading the pinned staging buffer.
-        if (slot->launched) {
-            cudaError_t e = cudaEventSynchronize(slot->done);
-            if (e != cudaSuccess) return cuda_fail(e, "wait for previous batch");
+    } else if (std::memcmp(slot->views.data(), hv.data(), vbytes) != 0) {
+        // Parameter updates apply to later launches only; a launch in flight
+        // keeps the views it started with.
+        auto a = std::make_unique<MarchArgs>();
+        for (size_t c = 0; c < slot->knodes.size(); ++c) {
+            cudaKernelNodeParams kp;
+            void *params[1];
+            cudaError_t e = chunk_params(ctx, vol, key, spec, *slot, hv.data(), static_cast<int>(c), *a, kp, params);
+            if (e == cudaSuccess) e = cudaGraphExecKernelNodeSetParams(slot->exec, slot->knodes[c], &kp);
+            if (e != cudaSuccess) return cuda_fail(e, "update batch graph");
         }
-        std::memcpy(slot->h_views, hv.data(), vbytes);
+        slot->views = hv;
     }
     cudaError_t e = cudaGraphLaunch(slot->exec, st);
     if (e != cudaSuccess) return cuda_fail(e, "graph launch");
     e = cudaEventRecord(slot->done, st);
     if (e != cudaSuccess) return cuda_fail(e, "graph event");
     slot->launched = true;
-    set_launch_count(1);
+    set_launch_count(static_cast<int>(slot->knodes.size()));
     return GBD_OK;
 }
 

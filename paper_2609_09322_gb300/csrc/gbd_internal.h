@@ -3,6 +3,7 @@
 // Nothing here is part of the public ABI (include/gbdart.h).
 #pragma once
 
+#include <climits>
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -22,12 +23,31 @@ constexpr int kMaxAxis = 4096;
 struct VolDev {
     const void *rec;          // record array (16-byte or 8-byte records)
     const int32_t *axis_off;  // n[0] + n[1] + n[2] entries
+    const int32_t *mtab;      // march tables, march_table_entries(n) entries (see below)
     long long epoch_stride;   // records per block (padded)
     int n[3];
     int M;
     int store;                // GBD_STORE_*
     int paired;               // 1: block b holds snapshots b-1 and b side by side
 };
+
+// March tables.  The march steps every axis towards increasing cell index:
+// an axis the view runs down is mirrored (cell k' = n - 1 - k) on the host.
+// For each axis the tables hold the forward terms off[0 .. n-1], then two
+// sentinels, then the reversed terms off[n-1 .. 0], then two sentinels.  A
+// step onto a sentinel is a step out of the box, and the sign bit of the
+// sentinel tells the march so; the second sentinel absorbs the read-ahead
+// of the next cell's term.
+constexpr int32_t kTabSentinel = INT32_MIN;
+__host__ __device__ inline int march_table_base(const int n[3], int axis)
+{
+    return axis == 0 ? 0 : (axis == 1 ? 2 * (n[0] + 2) : 2 * (n[0] + 2) + 2 * (n[1] + 2));
+}
+__host__ __device__ inline int march_table_entries(const int n[3]) { return 2 * (n[0] + n[1] + n[2] + 6); }
+
+// Bits of ViewDev::flags above the public GBD_BEAMING / GBD_LOOKBACK bits:
+// axis i is mirrored (the view's direction has s_hat_i < 0).
+constexpr uint32_t kFlagMirror0 = 1u << 8;
 
 // Per-view constants, computed on the host in float64 once per view, so that
 // the kernels need no float64 arithmetic (the FP64 rate of GB300 is 1/64 of
@@ -36,6 +56,8 @@ struct VolDev {
 // g_i = (x_i - origin_i) / dx_i, so cell faces sit at integers.
 //   fixed point: Q24.40 (int64, 2^-40 cells per unit) for positions,
 //                Q31.32 (int64, 2^-32 epochs per unit) for epoch coordinates.
+// Positions and directions are given in the mirrored frame of each mirrored
+// axis (g' = n - g, a' = -a), so every a_i, inv_a_i and w_i is >= 0.
 struct ViewDev {
     long long g0[3];   // pixel (0, 0) on the image plane, Q24.40
     long long gu[3];   // change per pixel column, Q24.40
@@ -55,24 +77,32 @@ struct ViewDev {
     float sh_lo[3];    // ... and the rounding residual (Doppler dot product)
     float expo;        // 2 - alpha
     float prefactor;   // (nu / nu'_0)^alpha
-    uint32_t flags;    // GBD_BEAMING | GBD_LOOKBACK
+    uint32_t flags;    // GBD_BEAMING | GBD_LOOKBACK | kFlagMirror0 << axis
 };
+
+// Views per march launch.  The views travel in the kernel's parameter space
+// (up to 32 KB on sm_70 and later with CUDA 12.1+), and each CTA works on one
+// view, so every per-view constant is uniform across the CTA and the compiler
+// keeps it in uniform registers instead of per-thread ones.  Larger batches
+// are split into several launches.
+constexpr int kViewsPerLaunch = 128;
 
 // One march launch: n_views views of one image geometry.
 struct MarchArgs {
     VolDev vol;
-    const ViewDev *views;     // device array, n_views entries
-    int n_views;
+    int n_views;              // views in this launch, 1 .. kViewsPerLaunch
     int width, height;
     int packet_w, packet_h;   // packet_w * packet_h == 32
     int tiles_x, tiles_y;     // packets per image row / column
-    long long total_items;    // n_views * tiles_x * tiles_y
+    int blocks_per_view;      // CTAs per view (set by plan_march)
+    int persistent;           // CTAs loop over their view's tile counter
     float *out;               // n_views * width * height floats
     uint32_t *samples;        // optional, same shape
-    int *queue;               // persistent mode: tile counter (zeroed before launch)
+    int *queue;               // persistent mode: one tile counter per view (zeroed before launch)
     int *error_word;          // checked builds: first bounds violation code
-    int persistent;
+    ViewDev views[kViewsPerLaunch];
 };
+static_assert(sizeof(MarchArgs) <= 32764, "march launch arguments exceed the kernel parameter limit");
 
 // One request of a served wave: its own volume, view, image and outputs.
 struct ReqDev {
@@ -80,30 +110,44 @@ struct ReqDev {
     ViewDev view;
     int width, height;
     int tiles_x, tiles_y;
-    long long tile_begin;     // first tile of this request in the wave's queue
+    int cta_begin;            // first CTA of this request in the launch
     float *out;               // device image of the request
     uint32_t *samples;        // optional per-pixel cell-sample counts
 };
 
-// A served wave: many requests in one persistent launch.
+// Requests per wave launch (parameter space, as for views); a larger wave is
+// several launches on its stream.
+constexpr int kReqsPerLaunch = 96;
+
+// One launch of a served wave: each request gets ceil(tiles / warps per CTA)
+// CTAs, one packet per warp.
 struct WaveArgs {
-    const ReqDev *reqs;       // device array, sorted by tile_begin
     int n_reqs;
     int packet_w, packet_h;
-    long long total_items;    // tiles of all requests
-    int *queue;               // tile counter (zeroed before launch)
+    int total_ctas;
     int *error_word;
+    ReqDev reqs[kReqsPerLaunch];  // sorted by cta_begin
 };
+static_assert(sizeof(WaveArgs) <= 32764, "wave launch arguments exceed the kernel parameter limit");
 
 // Launch configuration after defaults have been applied.
 struct LaunchCfg {
     int packet_w, packet_h, cta_warps, depth, persistent, regcap;
 };
 
-// Kernel entry points (march.cu, pack.cu).
-cudaError_t launch_march(const MarchArgs &a, const LaunchCfg &cfg, int num_sms, cudaStream_t stream);
-cudaError_t march_occupancy(const LaunchCfg &cfg, int store, int smem_bytes, int *blocks_per_sm);
-cudaError_t launch_wave(const WaveArgs &a, const LaunchCfg &cfg, int num_sms, cudaStream_t stream);
+// A planned kernel launch.
+struct KernelLaunch {
+    void *func;
+    dim3 grid, block;
+    int smem;
+};
+
+// Kernel entry points (march.cu, pack.cu).  plan_march picks the kernel and
+// grid for a filled MarchArgs and sets its blocks_per_view; launch_march plans
+// and launches.
+cudaError_t plan_march(MarchArgs &a, const LaunchCfg &cfg, int num_sms, KernelLaunch &k);
+cudaError_t launch_march(MarchArgs &a, const LaunchCfg &cfg, int num_sms, cudaStream_t stream);
+cudaError_t launch_wave(const WaveArgs &a, const LaunchCfg &cfg, cudaStream_t stream);
 
 struct PackArgs {
     const void *j;            // one epoch, [nz][ny][nx]

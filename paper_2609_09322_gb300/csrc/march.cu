@@ -5,21 +5,27 @@
 // A warp owns a packet of 32 neighbouring pixels (8x4 by default), so at each
 // step its lanes gather neighbouring cells of the bricked volume.
 //
-// Per ray (Sec. 2.4 traversal, Sec. 5.1 fast-forward, Eqs. 2, 6-9, 14, 19):
-//   * float64, once: pixel centre, slab entry/exit against the grid box, the
-//     s-window where the retarded time can reach a stored snapshot, the entry
-//     cell, and the epoch coordinate at the window start;
-//   * float32 per cell: the next face crossing of each axis recomputed from the
-//     integer cell index (never accumulated), the chord ds between the current
-//     and next crossing, the epoch coordinate at the chord midpoint, the two
-//     snapshot records, the Doppler boost of each, their linear interpolation,
-//     and a compensated float32 accumulation of value * ds.
+// Per view, on the host in float64: the constants of ViewDev (fixed-point
+// pixel positions, face spacings, epoch rates), with every axis the view runs
+// down mirrored so that the march always steps to increasing cell index.
+// Per ray (Sec. 2.4 traversal, Sec. 5.1 fast-forward, Eqs. 2, 6-9, 14, 19),
+// with no float64 on the device:
+//   * once: the pixel position in Q24.40 fixed point, an anchor at the later of
+//     the box entry and the window start where the retarded time can reach a
+//     stored snapshot, the anchor's cell, and the epoch coordinate there in
+//     Q31.32 fixed point;
+//   * per cell: the nearest next face crossing (each recomputed from its plane
+//     count, never accumulated), the chord ds from the previous one, the epoch
+//     coordinate at the chord midpoint, the two snapshot records, the Doppler
+//     boost of each, their linear interpolation, and a compensated float32
+//     accumulation of value * ds.
 // Cells are gathered DEPTH at a time: the traversal runs ahead, all loads of
 // the group are issued, then the group is evaluated, so each lane keeps up to
 // 2 * DEPTH independent loads in flight.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
+#include <algorithm>
 #include <cfloat>
 
 #include "gbd_internal.h"
@@ -163,13 +169,48 @@ __device__ __forceinline__ float fix_to_float(long long v, float inv_scale)
     return __ll2float_rn(v) * inv_scale;
 }
 
+// One term of the march tables at byte offset `cur` from `base`: shared
+// memory in the single-volume kernel, global memory when serving.
+template <bool SMEM>
+__device__ __forceinline__ int32_t tab_at(const int32_t *base, uint32_t cur)
+{
+    const int32_t *p = reinterpret_cast<const int32_t *>(reinterpret_cast<const char *>(base) + cur);
+    if (SMEM) return *p;
+    return __ldg(p);
+}
+
+// State of one axis of a ray: the next face crossing and what changes there.
+struct AxisState {
+    float nkf;      // planes from the anchor cell's lower face to the next crossing
+    float sn;       // s of the next crossing, relative to the anchor
+    float of;       // the anchor's offset inside its cell, times the face spacing
+    long long un;   // epoch coordinate at the next crossing, Q31.32
+    uint32_t cur;   // byte offset of the current cell's table term
+    int32_t o;      // table term of the current cell
+    int32_t pn;     // table term of the next cell (read ahead)
+};
+
+// Steps one axis of a ray into its next cell: the next crossing is recomputed
+// from the plane count (never accumulated), the epoch coordinate drops by the
+// exact per-plane amount, and the table term of the cell after is read ahead.
+template <bool SMEM>
+__device__ __forceinline__ void step_axis(AxisState &A, float inv_a, long long du, const int32_t *tab)
+{
+    A.nkf += 1.0f;
+    A.sn = fmaf(A.nkf, inv_a, -A.of);
+    A.un -= du;
+    A.o = A.pn;
+    A.cur += 4u;
+    A.pn = tab_at<SMEM>(tab, A.cur + 4u);
+}
+
 // Marches the ray of pixel (p, q) of one image and stores its value (and,
-// if cnt_img is set, its cell-sample count).  out_img points at the image.
-template <int STORE, int DEPTH, bool PAIRED>
+// if cnt_img is set, its cell-sample count).  out_img points at the image;
+// tab at the volume's march tables (shared memory when SMEM).
+template <int STORE, int DEPTH, bool PAIRED, bool SMEM>
 __device__ __forceinline__ void march_ray(const VolDev &vol, const ViewDev &V, int p, int q, int width, int height,
                                           float *out_img, uint32_t *cnt_img, int *err_word,
-                                          const int32_t *__restrict__ offx, const int32_t *__restrict__ offy,
-                                          const int32_t *__restrict__ offz)
+                                          const int32_t *__restrict__ tab)
 {
     using Rec = Record<STORE>;
     const bool in_image = (p < width) && (q < height);
@@ -177,7 +218,8 @@ __device__ __forceinline__ void march_ray(const VolDev &vol, const ViewDev &V, i
 
     // ---------------- ray setup, once per ray, no float64 ----------------
     // Pixel position on the image plane in grid-index units (Q24.40, exact
-    // integer arithmetic from the per-view constants).
+    // integer arithmetic from the per-view constants), in the frame where
+    // every axis is marched upwards.
     long long g0[3];
 #pragma unroll
     for (int i = 0; i < 3; ++i)
@@ -191,10 +233,8 @@ __device__ __forceinline__ void march_ray(const VolDev &vol, const ViewDev &V, i
     for (int i = 0; i < 3; ++i) {
         if (V.inv_a[i] != 0.f) {
             const float gf = fix_to_float(g0[i], kInv2p40);
-            const float t1 = -gf * V.inv_a[i];
-            const float t2 = (static_cast<float>(vol.n[i]) - gf) * V.inv_a[i];
-            s_in_e = fmaxf(s_in_e, fminf(t1, t2));
-            s_out_e = fminf(s_out_e, fmaxf(t1, t2));
+            s_in_e = fmaxf(s_in_e, -gf * V.inv_a[i]);
+            s_out_e = fminf(s_out_e, (static_cast<float>(vol.n[i]) - gf) * V.inv_a[i]);
         } else if (g0[i] < 0 || g0[i] >= (static_cast<long long>(vol.n[i]) << 40)) {
             alive = false;  // parallel to this axis and outside the box along it
         }
@@ -203,57 +243,95 @@ __device__ __forceinline__ void march_ray(const VolDev &vol, const ViewDev &V, i
     if (!(fminf(s_out_e, V.win_hi) > s_a - 1e-3f * (1.f + fabsf(s_a)))) alive = false;
     const float sa = alive ? s_a : 0.f;
 
-    // Anchor: the point s_a of the ray, in exact fixed point; its cell, the
-    // position o inside that cell, and per axis the face spacing along the
-    // ray (inv_a, Eq. 11), so that the crossing of the plane k cells above the
-    // anchor cell's lower face is at s_a + k inv_a - o inv_a.
-    int idx[3], step[3], nk[3];
-    float of[3];
-    long long un[3];
-    float s_lo_box = -3.0e38f, s_hi_box = 3.0e38f;  // box chord relative to the anchor
-    // epoch coordinate at the anchor: u_obs - kk s_a
+    // Anchor: the point s_a of the ray, in exact fixed point; its cell (k,
+    // clamped onto the grid), the position o inside that cell, and per axis
+    // the face spacing along the ray (inv_a, Eq. 11), so that the crossing of
+    // the plane nk cells above the cell's lower face is at nk inv_a - o inv_a.
     const long long u_a = V.u_obs - dd_mul_fix(sa, V.kk_hi, V.kk_lo, kTwo32);
+    AxisState ax[3];
+    float s_cur = -3.0e38f;  // the latest entry face of the anchor cell
+    long long u_cur = 0;
+#ifdef GBD_CHECKED
+    int kc[3];
+#endif
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
         const bool moving = V.inv_a[i] != 0.f;
         const long long ga = moving ? g0[i] + dd_mul_fix(sa, V.a_hi[i], V.a_lo[i], kTwo40) : g0[i];
         int k = static_cast<int>(ga >> 40);
         k = min(max(k, 0), vol.n[i] - 1);
-        idx[i] = k;
         const float o = fix_to_float(ga - (static_cast<long long>(k) << 40), kInv2p40);
-        step[i] = V.a_hi[i] > 0.f ? 1 : (V.a_hi[i] < 0.f ? -1 : 0);
-        nk[i] = step[i] > 0 ? 1 : 0;
-        of[i] = o * V.inv_a[i];
+        AxisState &A = ax[i];
+        A.nkf = 1.0f;
+        A.of = o * V.inv_a[i];
         if (moving) {
-            // box faces (planes 0 and n of this axis) relative to the anchor cell
-            const float t1 = fmaf(static_cast<float>(-k), V.inv_a[i], -of[i]);
-            const float t2 = fmaf(static_cast<float>(vol.n[i] - k), V.inv_a[i], -of[i]);
-            s_lo_box = fmaxf(s_lo_box, fminf(t1, t2));
-            s_hi_box = fminf(s_hi_box, fmaxf(t1, t2));
+            A.sn = V.inv_a[i] - A.of;
+            A.un = u_a - dd_mul_fix(1.0f - o, V.w_hi[i], V.w_lo[i], kTwo32);
+            // the anchor cell's entry face along this axis (plane nk = 0)
+            if (-A.of > s_cur) {
+                s_cur = -A.of;
+                u_cur = A.un + V.du[i];
+            }
+        } else {
+            A.sn = 3.0e38f;      // never the nearest face ...
+            A.un = LLONG_MIN / 2;  // ... and ends the ray if it ever were
         }
-        // u at the next crossing: u_a - kk (nk - o) / a_i
-        un[i] = u_a - dd_mul_fix(static_cast<float>(nk[i]) - o, V.w_hi[i], V.w_lo[i], kTwo32);
+        const bool mirrored = (V.flags & (kFlagMirror0 << i)) != 0u;
+        A.cur = 4u * static_cast<uint32_t>(march_table_base(vol.n, i) + (mirrored ? vol.n[i] + 2 : 0) + k);
+        A.o = 0;
+        A.pn = 0;
+        if (alive) {
+            A.o = tab_at<SMEM>(tab, A.cur);
+            A.pn = tab_at<SMEM>(tab, A.cur + 4u);
+        }
+#ifdef GBD_CHECKED
+        kc[i] = mirrored ? vol.n[i] - 1 - k : k;
+#endif
     }
-    if (!(s_hi_box > s_lo_box)) alive = false;
-    float sn[3];
-    float s_cur = -3.0e38f;
-    long long u_cur = 0;
-#pragma unroll
-    for (int i = 0; i < 3; ++i) {
-        sn[i] = step[i] == 0 ? 3.0e38f : fmaf(static_cast<float>(nk[i]), V.inv_a[i], -of[i]);
-        if (step[i] != 0) {
-            // the anchor cell's own entry face: the latest of its three
-            const float se = fmaf(static_cast<float>(nk[i] - step[i]), V.inv_a[i], -of[i]);
-            if (se > s_cur) {
-                s_cur = se;
-                u_cur = un[i] + V.du[i];  // the entry plane is one plane behind the next one
+    const float ia0 = V.inv_a[0], ia1 = V.inv_a[1], ia2 = V.inv_a[2];
+    const long long du0 = V.du[0], du1 = V.du[1], du2 = V.du[2];
+#ifdef GBD_CHECKED
+    const int kd0 = (V.flags & kFlagMirror0) ? -1 : 1;
+    const int kd1 = (V.flags & (kFlagMirror0 << 1)) ? -1 : 1;
+    const int kd2 = (V.flags & (kFlagMirror0 << 2)) ? -1 : 1;
+#endif
+
+    // Leading empty chords: when the anchor cell was clamped onto the grid, or
+    // the anchor sits on a face, the ray can leave a cell along one axis before
+    // it has entered it along another.  Those cells are stepped through until
+    // the nearest exit lies past the latest entry; from there on the exits
+    // only increase, so every chord of the march proper starts at the end of
+    // the one before.  Each step moves one table cursor up, and a sentinel
+    // stops the ray at the box face, so the loop is bounded by the grid.
+    if (alive) {
+        for (int guard = vol.n[0] + vol.n[1] + vol.n[2] + 4; guard > 0; --guard) {
+            const bool x0 = ax[0].sn <= ax[1].sn && ax[0].sn <= ax[2].sn;
+            const bool x1 = !x0 && ax[1].sn <= ax[2].sn;
+            const float s_exit = x0 ? ax[0].sn : (x1 ? ax[1].sn : ax[2].sn);
+            if (s_exit > s_cur) break;
+            if (x0) {
+                step_axis<SMEM>(ax[0], ia0, du0, tab);
+#ifdef GBD_CHECKED
+                kc[0] += kd0;
+#endif
+            } else if (x1) {
+                step_axis<SMEM>(ax[1], ia1, du1, tab);
+#ifdef GBD_CHECKED
+                kc[1] += kd1;
+#endif
+            } else {
+                step_axis<SMEM>(ax[2], ia2, du2, tab);
+#ifdef GBD_CHECKED
+                kc[2] += kd2;
+#endif
+            }
+            if ((ax[0].o | ax[1].o | ax[2].o) < 0) {
+                alive = false;
+                break;
             }
         }
     }
-    // The march never counts a chord outside the box: a start cell that was
-    // clamped onto the grid yields empty chords until the ray enters.
-    s_cur = fmaxf(s_cur, s_lo_box);
-    const long long u_lo = -(1LL << 32);                          // u = -1
+    const long long u_lo = -(1LL << 32);  // u = -1
     const int Mm1 = vol.M - 1;
 
     BoostConsts bc;
@@ -262,27 +340,16 @@ __device__ __forceinline__ void march_ray(const VolDev &vol, const ViewDev &V, i
     bc.expo = V.expo;
     bc.beaming = (V.flags & GBD_BEAMING) != 0u;
 
-    // Table terms of the current cell, and of the next cell along each axis
-    // (prefetched so that a step never waits on shared memory).
-    int32_t ox = 0, oy = 0, oz = 0, px = 0, py = 0, pz = 0;
-    if (alive) {
-        ox = offx[idx[0]];
-        oy = offy[idx[1]];
-        oz = offz[idx[2]];
-        px = offx[min(max(idx[0] + step[0], 0), vol.n[0] - 1)];
-        py = offy[min(max(idx[1] + step[1], 0), vol.n[1] - 1)];
-        pz = offz[min(max(idx[2] + step[2], 0), vol.n[2] - 1)];
-    }
     const long long es = vol.epoch_stride;
     const void *recs = vol.rec;
 
     float acc = 0.f, comp = 0.f;
     uint32_t count = 0;
-    // A ray crosses at most n_x + n_y + n_z cells; the budget bounds the loop
-    // whatever the floating-point crossings do.
-    int steps_left = vol.n[0] + vol.n[1] + vol.n[2] + 4;
 
     // ---------------- the march, float32 per cell ----------------
+    // Per cell: the nearest face, the chord from the previous exit, the epoch
+    // coordinate at the chord midpoint, and one step of the exit axis.  The
+    // ray ends past the last time that reaches a snapshot or at a sentinel.
     while (__any_sync(kFull, alive)) {
         long long off[DEPTH];
         float wgt[DEPTH], dsv[DEPTH];
@@ -297,10 +364,10 @@ __device__ __forceinline__ void march_ray(const VolDev &vol, const ViewDev &V, i
             if (alive) {
                 // The cell is left through the nearest face; ties go to the
                 // lowest axis (the zero-length chord that follows adds nothing).
-                const bool x0 = sn[0] <= sn[1] && sn[0] <= sn[2];
-                const bool x1 = !x0 && sn[1] <= sn[2];
-                const float s_exit = fminf(x0 ? sn[0] : (x1 ? sn[1] : sn[2]), s_hi_box);
-                const long long u_exit = x0 ? un[0] : (x1 ? un[1] : un[2]);
+                const bool x0 = ax[0].sn <= ax[1].sn && ax[0].sn <= ax[2].sn;
+                const bool x1 = !x0 && ax[1].sn <= ax[2].sn;
+                const float s_exit = x0 ? ax[0].sn : (x1 ? ax[1].sn : ax[2].sn);
+                const long long u_exit = x0 ? ax[0].un : (x1 ? ax[1].un : ax[2].un);
                 const float ds = s_exit - s_cur;
                 // epoch coordinate at the chord midpoint: m_bar + w, w in [0, 1)
                 const long long um = (u_cur + u_exit) >> 1;
@@ -312,66 +379,40 @@ __device__ __forceinline__ void march_ray(const VolDev &vol, const ViewDev &V, i
                     has_lo[d] = mb >= 0;
                     has_hi[d] = (mb < Mm1) && (frac != 0u);
 #ifdef GBD_CHECKED
-                    if ((has_lo[d] && !check_cell(vol, err_word, idx[0], idx[1], idx[2], mb)) ||
-                        (has_hi[d] && !check_cell(vol, err_word, idx[0], idx[1], idx[2], mb + 1))) {
+                    if ((has_lo[d] && !check_cell(vol, err_word, kc[0], kc[1], kc[2], mb)) ||
+                        (has_hi[d] && !check_cell(vol, err_word, kc[0], kc[1], kc[2], mb + 1))) {
                         has_lo[d] = has_hi[d] = false;
                     }
 #endif
+                    const int sum = ax[0].o + ax[1].o + ax[2].o;
                     // unpaired: snapshot m at block m; paired: snapshots mb and
                     // mb + 1 side by side in block mb + 1
-                    off[d] = PAIRED ? static_cast<long long>(mb + 1) * es + 2LL * (ox + oy + oz)
-                                    : static_cast<long long>(mb) * es + (ox + oy + oz);
+                    off[d] = PAIRED ? static_cast<long long>(mb + 1) * es + 2LL * sum
+                                    : static_cast<long long>(mb) * es + sum;
                     wgt[d] = w;
                     dsv[d] = ds;
                 }
+                if (x0) {
+                    step_axis<SMEM>(ax[0], ia0, du0, tab);
+#ifdef GBD_CHECKED
+                    kc[0] += kd0;
+#endif
+                } else if (x1) {
+                    step_axis<SMEM>(ax[1], ia1, du1, tab);
+#ifdef GBD_CHECKED
+                    kc[1] += kd1;
+#endif
+                } else {
+                    step_axis<SMEM>(ax[2], ia2, du2, tab);
+#ifdef GBD_CHECKED
+                    kc[2] += kd2;
+#endif
+                }
+                s_cur = s_exit;
+                u_cur = u_exit;
                 // Past the last time that reaches a snapshot, or out of the
                 // box: nothing further along the ray can contribute.
-                if (u_exit <= u_lo || s_exit >= s_hi_box || --steps_left <= 0) {
-                    alive = false;
-                } else if (x0) {
-                    const int k = idx[0] + step[0];
-                    if (step[0] == 0 || k < 0 || k >= vol.n[0]) {
-                        alive = false;
-                    } else {
-                        idx[0] = k;
-                        nk[0] += step[0];
-                        sn[0] = fmaf(static_cast<float>(nk[0]), V.inv_a[0], -of[0]);
-                        un[0] -= V.du[0];
-                        ox = px;
-                        px = offx[min(max(k + step[0], 0), vol.n[0] - 1)];
-                    }
-                } else if (x1) {
-                    const int k = idx[1] + step[1];
-                    if (step[1] == 0 || k < 0 || k >= vol.n[1]) {
-                        alive = false;
-                    } else {
-                        idx[1] = k;
-                        nk[1] += step[1];
-                        sn[1] = fmaf(static_cast<float>(nk[1]), V.inv_a[1], -of[1]);
-                        un[1] -= V.du[1];
-                        oy = py;
-                        py = offy[min(max(k + step[1], 0), vol.n[1] - 1)];
-                    }
-                } else {
-                    const int k = idx[2] + step[2];
-                    if (step[2] == 0 || k < 0 || k >= vol.n[2]) {
-                        alive = false;
-                    } else {
-                        idx[2] = k;
-                        nk[2] += step[2];
-                        sn[2] = fmaf(static_cast<float>(nk[2]), V.inv_a[2], -of[2]);
-                        un[2] -= V.du[2];
-                        oz = pz;
-                        pz = offz[min(max(k + step[2], 0), vol.n[2] - 1)];
-                    }
-                }
-                // the next chord starts where this one ended (an empty chord
-                // before the ray enters the box leaves the start unchanged,
-                // with the epoch coordinate that belongs to it)
-                if (s_exit > s_cur) {
-                    s_cur = s_exit;
-                    u_cur = u_exit;
-                }
+                alive = u_exit > u_lo && (ax[0].o | ax[1].o | ax[2].o) >= 0;
             }
         }
         typename Rec::T rlo[DEPTH], rhi[DEPTH];
@@ -410,87 +451,86 @@ __device__ __forceinline__ void march_ray(const VolDev &vol, const ViewDev &V, i
 
 // MINB = 1 leaves the register count to the compiler; MINB = 3 asks for
 // three 256-thread CTAs per SM (at most 80 registers per thread).
+//
+// Each CTA works on one view (blockIdx.x / blocks_per_view), one packet per
+// warp: its tile directly, or, persistent, tiles pulled from the view's
+// counter until none are left.
 template <int STORE, int DEPTH, int MINB, bool PAIRED>
-__global__ void __launch_bounds__(256, MINB) march_kernel(const MarchArgs a)
+__global__ void __launch_bounds__(256, MINB) march_kernel(const __grid_constant__ MarchArgs a)
 {
-    extern __shared__ int32_t s_off[];
-    const int nx = a.vol.n[0], ny = a.vol.n[1], nz = a.vol.n[2];
-    const int ntab = nx + ny + nz;
-    for (int i = threadIdx.x; i < ntab; i += blockDim.x) s_off[i] = a.vol.axis_off[i];
+    extern __shared__ int32_t s_tab[];
+    const int ntab = march_table_entries(a.vol.n);
+    for (int i = threadIdx.x; i < ntab; i += blockDim.x) s_tab[i] = a.vol.mtab[i];
     __syncthreads();
-    const int32_t *offx = s_off;
-    const int32_t *offy = s_off + nx;
-    const int32_t *offz = s_off + nx + ny;
 
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const int wpc = blockDim.x >> 5;
-    const long long tiles_per_view = static_cast<long long>(a.tiles_x) * a.tiles_y;
-    long long item = static_cast<long long>(blockIdx.x) * wpc + warp;
+    const int vi = static_cast<int>(blockIdx.x) / a.blocks_per_view;
+    const int cb = static_cast<int>(blockIdx.x) - vi * a.blocks_per_view;
+    const ViewDev &V = a.views[vi];
+    const int tiles = a.tiles_x * a.tiles_y;
+    const long long img = static_cast<long long>(vi) * a.width * a.height;
+    float *out = a.out + img;
+    uint32_t *cnt = a.samples ? a.samples + img : nullptr;
+    int tile = cb * wpc + warp;
     for (;;) {
         if (a.persistent) {
             int it = 0;
-            if (lane == 0) it = atomicAdd(a.queue, 1);
-            item = __shfl_sync(kFull, it, 0);
+            if (lane == 0) it = atomicAdd(a.queue + vi, 1);
+            tile = __shfl_sync(kFull, it, 0);
         }
-        if (item >= a.total_items) break;
-        const int vi = static_cast<int>(item / tiles_per_view);
-        const int tile = static_cast<int>(item - static_cast<long long>(vi) * tiles_per_view);
+        if (tile >= tiles) break;
         const int tx = tile % a.tiles_x;
         const int ty = tile / a.tiles_x;
         const int p = tx * a.packet_w + lane % a.packet_w;
         const int q = ty * a.packet_h + lane / a.packet_w;
-        const long long img = static_cast<long long>(vi) * a.width * a.height;
-        march_ray<STORE, DEPTH, PAIRED>(a.vol, a.views[vi], p, q, a.width, a.height, a.out + img,
-                                        a.samples ? a.samples + img : nullptr, a.error_word, offx, offy, offz);
+        march_ray<STORE, DEPTH, PAIRED, true>(a.vol, V, p, q, a.width, a.height, out, cnt, a.error_word, s_tab);
         if (!a.persistent) break;
     }
 }
 
-// Serving: one persistent launch over the tiles of many requests, each with
-// its own volume (float32 or bfloat16/float16 records), view and image.  The
-// layout tables are read from global memory (they differ per request); every
-// ray runs the same march_ray as the single-volume kernel, so a request's
-// pixels are the same whether it is served alone or in a mix.
+// Serving: one launch over the tiles of many requests, each with its own
+// volume (float32 or bfloat16/float16 records), view and image.  A CTA finds
+// its request by binary search over the requests' first CTAs (uniform across
+// the CTA).  The march tables are read from global memory (they differ per
+// request); every ray runs the same march_ray as the single-volume kernel, so
+// a request's pixels are the same whether it is served alone or in a mix.
 template <int DEPTH, int MINB>
-__global__ void __launch_bounds__(256, MINB) wave_kernel(const WaveArgs a)
+__global__ void __launch_bounds__(256, MINB) wave_kernel(const __grid_constant__ WaveArgs a)
 {
     const int lane = threadIdx.x & 31;
-    for (;;) {
-        int it = 0;
-        if (lane == 0) it = atomicAdd(a.queue, 1);
-        const long long item = __shfl_sync(kFull, it, 0);
-        if (item >= a.total_items) break;
-        int lo = 0, hi = a.n_reqs - 1;  // last request whose first tile is <= item
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (a.reqs[mid].tile_begin <= item) lo = mid;
-            else hi = mid - 1;
-        }
-        const ReqDev &R = a.reqs[lo];
-        const int tile = static_cast<int>(item - R.tile_begin);
-        const int tx = tile % R.tiles_x;
-        const int ty = tile / R.tiles_x;
-        const int p = tx * a.packet_w + lane % a.packet_w;
-        const int q = ty * a.packet_h + lane / a.packet_w;
-        const int32_t *tab = R.vol.axis_off;
-        const int32_t *ty_tab = tab + R.vol.n[0];
-        const int32_t *tz_tab = ty_tab + R.vol.n[1];
-        if (R.vol.store == GBD_STORE_F32) {
-            if (R.vol.paired)
-                march_ray<GBD_STORE_F32, DEPTH, true>(R.vol, R.view, p, q, R.width, R.height, R.out, R.samples,
-                                                      a.error_word, tab, ty_tab, tz_tab);
-            else
-                march_ray<GBD_STORE_F32, DEPTH, false>(R.vol, R.view, p, q, R.width, R.height, R.out, R.samples,
-                                                       a.error_word, tab, ty_tab, tz_tab);
-        } else {
-            if (R.vol.paired)
-                march_ray<GBD_STORE_BF16_F16U, DEPTH, true>(R.vol, R.view, p, q, R.width, R.height, R.out,
-                                                            R.samples, a.error_word, tab, ty_tab, tz_tab);
-            else
-                march_ray<GBD_STORE_BF16_F16U, DEPTH, false>(R.vol, R.view, p, q, R.width, R.height, R.out,
-                                                             R.samples, a.error_word, tab, ty_tab, tz_tab);
-        }
+    const int warp = threadIdx.x >> 5;
+    const int wpc = blockDim.x >> 5;
+    const int b = static_cast<int>(blockIdx.x);
+    int lo = 0, hi = a.n_reqs - 1;  // last request whose first CTA is <= b
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (a.reqs[mid].cta_begin <= b) lo = mid;
+        else hi = mid - 1;
+    }
+    const ReqDev &R = a.reqs[lo];
+    const int tile = (b - R.cta_begin) * wpc + warp;
+    if (tile >= R.tiles_x * R.tiles_y) return;
+    const int tx = tile % R.tiles_x;
+    const int ty = tile / R.tiles_x;
+    const int p = tx * a.packet_w + lane % a.packet_w;
+    const int q = ty * a.packet_h + lane / a.packet_w;
+    const int32_t *tab = R.vol.mtab;
+    if (R.vol.store == GBD_STORE_F32) {
+        if (R.vol.paired)
+            march_ray<GBD_STORE_F32, DEPTH, true, false>(R.vol, R.view, p, q, R.width, R.height, R.out, R.samples,
+                                                         a.error_word, tab);
+        else
+            march_ray<GBD_STORE_F32, DEPTH, false, false>(R.vol, R.view, p, q, R.width, R.height, R.out, R.samples,
+                                                          a.error_word, tab);
+    } else {
+        if (R.vol.paired)
+            march_ray<GBD_STORE_BF16_F16U, DEPTH, true, false>(R.vol, R.view, p, q, R.width, R.height, R.out,
+                                                               R.samples, a.error_word, tab);
+        else
+            march_ray<GBD_STORE_BF16_F16U, DEPTH, false, false>(R.vol, R.view, p, q, R.width, R.height, R.out,
+                                                                R.samples, a.error_word, tab);
     }
 }
 
@@ -536,54 +576,55 @@ void *select_wave(int depth, int capped)
 
 }  // namespace
 
-cudaError_t launch_wave(const WaveArgs &a, const LaunchCfg &cfg, int num_sms, cudaStream_t stream)
+cudaError_t launch_wave(const WaveArgs &a, const LaunchCfg &cfg, cudaStream_t stream)
 {
     void *k = select_wave(cfg.depth, cfg.regcap);
     if (!k) return cudaErrorInvalidValue;
-    const int threads = 32 * cfg.cta_warps;
-    int per_sm = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, threads, 0);
-    if (e != cudaSuccess) return e;
-    if (per_sm < 1) per_sm = 1;
-    long long blocks = static_cast<long long>(per_sm) * num_sms;
-    const long long needed = (a.total_items + cfg.cta_warps - 1) / cfg.cta_warps;
-    if (blocks > needed) blocks = needed;
-    if (blocks < 1) return cudaSuccess;
-    WaveArgs args = a;
-    void *params[] = {&args};
-    return cudaLaunchKernel(k, dim3(static_cast<unsigned>(blocks)), dim3(threads), params, 0, stream);
+    if (a.total_ctas < 1) return cudaSuccess;
+    void *params[] = {const_cast<WaveArgs *>(&a)};
+    return cudaLaunchKernel(k, dim3(static_cast<unsigned>(a.total_ctas)), dim3(32 * cfg.cta_warps), params, 0,
+                            stream);
 }
 
-cudaError_t march_occupancy(const LaunchCfg &cfg, int store, int smem_bytes, int *blocks_per_sm)
-{
-    void *k = select_kernel(store, cfg.depth, cfg.regcap, 0);
-    if (!k) return cudaErrorInvalidValue;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k, 32 * cfg.cta_warps, smem_bytes);
-}
-
-cudaError_t launch_march(const MarchArgs &a, const LaunchCfg &cfg, int num_sms, cudaStream_t stream)
+cudaError_t plan_march(MarchArgs &a, const LaunchCfg &cfg, int num_sms, KernelLaunch &L)
 {
     void *k = select_kernel(a.vol.store, cfg.depth, cfg.regcap, a.vol.paired);
-    if (!k) return cudaErrorInvalidValue;
+    if (!k || a.n_views < 1 || a.n_views > kViewsPerLaunch) return cudaErrorInvalidValue;
     const int threads = 32 * cfg.cta_warps;
-    const int smem = static_cast<int>(sizeof(int32_t)) * (a.vol.n[0] + a.vol.n[1] + a.vol.n[2]);
-    long long blocks;
+    const int smem = static_cast<int>(sizeof(int32_t)) * march_table_entries(a.vol.n);
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+    }
+    const long long tiles = static_cast<long long>(a.tiles_x) * a.tiles_y;
+    const long long needed = (tiles + cfg.cta_warps - 1) / cfg.cta_warps;
+    long long per_view = needed;
     if (a.persistent) {
+        // enough CTAs to fill the GPU once, shared out over the views
         int per_sm = 0;
         cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, threads, smem);
         if (e != cudaSuccess) return e;
         if (per_sm < 1) per_sm = 1;
-        blocks = static_cast<long long>(per_sm) * num_sms;
-        const long long needed = (a.total_items + cfg.cta_warps - 1) / cfg.cta_warps;
-        if (blocks > needed) blocks = needed;
-    } else {
-        blocks = (a.total_items + cfg.cta_warps - 1) / cfg.cta_warps;
+        const long long resident = static_cast<long long>(per_sm) * num_sms;
+        per_view = std::min(needed, std::max(1LL, (resident + a.n_views - 1) / a.n_views));
     }
-    if (blocks < 1) return cudaSuccess;
-    if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
-    MarchArgs args = a;
-    void *params[] = {&args};
-    return cudaLaunchKernel(k, dim3(static_cast<unsigned>(blocks)), dim3(threads), params, smem, stream);
+    const long long blocks = per_view * a.n_views;
+    if (blocks < 1 || blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
+    a.blocks_per_view = static_cast<int>(per_view);
+    L.func = k;
+    L.grid = dim3(static_cast<unsigned>(blocks));
+    L.block = dim3(threads);
+    L.smem = smem;
+    return cudaSuccess;
+}
+
+cudaError_t launch_march(MarchArgs &a, const LaunchCfg &cfg, int num_sms, cudaStream_t stream)
+{
+    KernelLaunch L;
+    cudaError_t e = plan_march(a, cfg, num_sms, L);
+    if (e != cudaSuccess) return e;
+    void *params[] = {&a};
+    return cudaLaunchKernel(L.func, L.grid, L.block, params, L.smem, stream);
 }
 
 }  // namespace gbd

@@ -1,7 +1,7 @@
 // noalloc.cu -- batch render that allocates no memory.
 //
-// gbd_render_batch keeps its view table and tile counter in memory it
-// allocates (a cached graph's buffer, or stream-ordered scratch).  Some
+// gbd_render_batch keeps its per-view tile counters in memory it allocates
+// (a cached graph's buffer, or stream-ordered scratch).  Some
 // callers cannot let a library allocate device memory while they render:
 // applications that hand the whole device to their own allocator or memory
 // pool up front (a cudaMalloc inside the library would fail, or break their
@@ -20,19 +20,18 @@ namespace gbd {
 namespace {
 
 constexpr int kNoAllocMaxViews = GBD_NOALLOC_MAX_VIEWS;
-constexpr size_t kViewTableBytes = sizeof(ViewDev) * kNoAllocMaxViews;
-constexpr size_t kCounterOffset = (kViewTableBytes + 255) / 256 * 256;
-constexpr size_t kScratchBytes = kCounterOffset + 256;
+constexpr size_t kScratchBytes = sizeof(int) * kNoAllocMaxViews;  // one tile counter per view
 constexpr int kMaxDevices = 64;
 
-// Device scratch: the view table, then the tile counter of the persistent
-// grid.  In host code this name is only a stand-in for the symbol; its device
-// address comes from cudaGetSymbolAddress.
+// Device scratch: the tile counters of the persistent grid (the views travel
+// in the launch parameters).  In host code this name is only a stand-in for
+// the symbol; its device address comes from cudaGetSymbolAddress.
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
-std::mutex g_mu;                          // guards the two arrays below
+std::mutex g_mu;                          // guards the arrays below
 void *g_scratch_addr[kMaxDevices] = {};   // device address of g_scratch, per device
-ViewDev g_host_views[kNoAllocMaxViews];   // host staging of the view table
+ViewDev g_host_views[kNoAllocMaxViews];   // the views, set up on the host
+MarchArgs g_args;                         // launch arguments (about 28 KB: not on the stack)
 
 // Looks up the device address of the scratch array on the current device
 // (once per device; the caller holds g_mu and has made `dev` current).
@@ -81,16 +80,14 @@ extern "C" int gbd_render_batch_noalloc(gbd_ctx *ctx, gbd_volume vid, const gbd_
         if ((rc = make_view(*vol, views[k], spec->width, spec->height, spec->fov_u, spec->fov_v, g_host_views[k])))
             return rc;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    ViewDev *d_views = reinterpret_cast<ViewDev *>(scratch);
-    int *queue = reinterpret_cast<int *>(scratch + kCounterOffset);
-    // The host staging array is pageable: the copy has consumed it when the
-    // call returns, so the next call may refill it.
-    cudaError_t e = cudaMemcpyAsync(d_views, g_host_views, sizeof(ViewDev) * n, cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(queue, 0, 256, st);  // the tile counter starts at zero
-    MarchArgs a;
-    fill_args(a, *vol, d_views, n, *spec, spec->out, spec->samples, queue, cfg, ctx->err_word);
-    if (e == cudaSuccess) e = launch_march(a, cfg, ctx->num_sms, st);
+    int *queue = reinterpret_cast<int *>(scratch);
+    cudaError_t e = cudaMemsetAsync(queue, 0, sizeof(int) * static_cast<size_t>(n), st);  // counters start at zero
+    const int chunks = march_chunks(n);
+    for (int c = 0; c < chunks && e == cudaSuccess; ++c) {
+        fill_args(g_args, *vol, g_host_views, n, c, *spec, spec->out, spec->samples, queue, cfg, ctx->err_word);
+        e = launch_march(g_args, cfg, ctx->num_sms, st);
+    }
     if (e != cudaSuccess) return cuda_fail(e, "no-alloc batch launch");
-    set_launch_count(1);
+    set_launch_count(chunks);
     return GBD_OK;
 }

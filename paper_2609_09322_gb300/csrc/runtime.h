@@ -96,7 +96,10 @@ int make_view(const Volume &vol, const gbd_view &v, int width, int height, doubl
 VolDev vol_dev(const Volume &v);
 LaunchCfg resolve_launch(const gbd_launch *l);
 int check_launch(const LaunchCfg &c);
-void fill_args(MarchArgs &a, const Volume &vol, const ViewDev *d_views, int n, const gbd_image_spec &s,
+// A batch of n views runs as march_chunks(n) launches; fill_args sets up the
+// arguments of launch c from the host view array hv.
+int march_chunks(int n);
+void fill_args(MarchArgs &a, const Volume &vol, const ViewDev *hv, int n, int c, const gbd_image_spec &s,
                float *out, uint32_t *samples, int *queue, const LaunchCfg &cfg, int *err_word);
 bool build_layout(const int n[3], int B, int S, std::vector<int32_t> &tab, long long &epoch_stride, int morton_cells);
 void destroy_graph_cache(GraphCache *g);

@@ -2,9 +2,9 @@
 //
 // Requests (one view of one resident volume, any image size, any storage)
 // are queued by gbd_submit.  A scheduler thread admits queued requests into
-// waves as request slots and HBM budget free up, and launches each wave as one
-// persistent multi-request kernel (wave_kernel in march.cu) on one of several
-// streams.  Up to `max_waves` waves are on the GPU at once, so a wave formed
+// waves as request slots and HBM budget free up, and launches each wave as
+// multi-request kernels (wave_kernel in march.cu, up to kReqsPerLaunch
+// requests per launch) on one of several streams.  Up to `max_waves` waves are on the GPU at once, so a wave formed
 // from requests that arrived while earlier ones were running starts filling
 // SMs as soon as the earlier wave's tail drains.  Completion is signalled by a
 // host-function callback; waiting is always bounded by the caller's timeout
@@ -57,8 +57,7 @@ struct WaveSlot {
     int index = 0;
     cudaStream_t stream = nullptr;
     cudaEvent_t ev_start = nullptr, ev_stop = nullptr;
-    ReqDev *h_desc = nullptr;  // pinned host staging of the request table
-    char *d_buf = nullptr;     // device: request table, then the tile counter
+    WaveArgs *args = nullptr;  // launch arguments (about 30 KB), reused per launch
     std::vector<uint64_t> tickets;
     std::atomic<bool> gpu_done{false};
     double t_gpu_done = 0;
@@ -194,45 +193,41 @@ bool Server::launch_wave_from_queue(WaveSlot &w)
     char *d_img = nullptr;
     cudaError_t e = cudaSuccess;
     if (host_img_bytes) e = cudaMallocAsync(reinterpret_cast<void **>(&d_img), host_img_bytes, w.stream);
-    long long tile_begin = 0;
     uint64_t img_off = 0;
     std::vector<uint64_t> host_off(take.size(), 0);
-    for (size_t i = 0; i < take.size(); ++i) {
-        ServedReq &r = *take[i];
-        ReqDev &d = w.h_desc[i];
-        std::memset(&d, 0, sizeof(d));
-        d.vol = r.vdev;
-        d.view = r.view;
-        d.width = r.spec.width;
-        d.height = r.spec.height;
-        d.tiles_x = (r.spec.width + launch.packet_w - 1) / launch.packet_w;
-        d.tiles_y = (r.spec.height + launch.packet_h - 1) / launch.packet_h;
-        d.tile_begin = tile_begin;
-        tile_begin += static_cast<long long>(d.tiles_x) * d.tiles_y;
-        if (r.spec.out_on_host) {
-            d.out = reinterpret_cast<float *>(d_img + img_off);
-            host_off[i] = img_off;
-            img_off += static_cast<uint64_t>(r.spec.width) * r.spec.height * 4;
-        } else {
-            d.out = r.spec.out;
-            d.samples = r.spec.samples;
-        }
-    }
-    const size_t desc_bytes = sizeof(ReqDev) * take.size();
-    const size_t q_off = (sizeof(ReqDev) * cfg.max_requests_per_wave + 255) / 256 * 256;
-    if (e == cudaSuccess) e = cudaMemcpyAsync(w.d_buf, w.h_desc, desc_bytes, cudaMemcpyHostToDevice, w.stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(w.d_buf + q_off, 0, 256, w.stream);
     if (e == cudaSuccess) e = cudaEventRecord(w.ev_start, w.stream);
-    WaveArgs a;
-    std::memset(&a, 0, sizeof(a));
-    a.reqs = reinterpret_cast<const ReqDev *>(w.d_buf);
-    a.n_reqs = static_cast<int>(take.size());
-    a.packet_w = launch.packet_w;
-    a.packet_h = launch.packet_h;
-    a.total_items = tile_begin;
-    a.queue = reinterpret_cast<int *>(w.d_buf + q_off);
-    a.error_word = ctx->err_word;
-    if (e == cudaSuccess) e = launch_wave(a, launch, ctx->num_sms, w.stream);
+    for (size_t first = 0; first < take.size() && e == cudaSuccess; first += kReqsPerLaunch) {
+        const size_t cnt = std::min<size_t>(kReqsPerLaunch, take.size() - first);
+        WaveArgs &a = *w.args;
+        std::memset(&a, 0, sizeof(a));
+        int cta_begin = 0;
+        for (size_t i = 0; i < cnt; ++i) {
+            ServedReq &r = *take[first + i];
+            ReqDev &d = a.reqs[i];
+            d.vol = r.vdev;
+            d.view = r.view;
+            d.width = r.spec.width;
+            d.height = r.spec.height;
+            d.tiles_x = (r.spec.width + launch.packet_w - 1) / launch.packet_w;
+            d.tiles_y = (r.spec.height + launch.packet_h - 1) / launch.packet_h;
+            d.cta_begin = cta_begin;
+            cta_begin += (d.tiles_x * d.tiles_y + launch.cta_warps - 1) / launch.cta_warps;
+            if (r.spec.out_on_host) {
+                d.out = reinterpret_cast<float *>(d_img + img_off);
+                host_off[first + i] = img_off;
+                img_off += static_cast<uint64_t>(r.spec.width) * r.spec.height * 4;
+            } else {
+                d.out = r.spec.out;
+                d.samples = r.spec.samples;
+            }
+        }
+        a.n_reqs = static_cast<int>(cnt);
+        a.packet_w = launch.packet_w;
+        a.packet_h = launch.packet_h;
+        a.total_ctas = cta_begin;
+        a.error_word = ctx->err_word;
+        e = launch_wave(a, launch, w.stream);
+    }
     if (e == cudaSuccess) e = cudaEventRecord(w.ev_stop, w.stream);
     for (size_t i = 0; i < take.size() && e == cudaSuccess; ++i) {
         ServedReq &r = *take[i];
@@ -329,7 +324,6 @@ int serve_start(Ctx &ctx, const gbd_serve_config *c)
     s->launch = lc;
     const uint64_t free_budget = ctx.budget > ctx.used ? ctx.budget - ctx.used : 0;
     s->request_budget = d.request_budget_bytes ? std::min<uint64_t>(d.request_budget_bytes, free_budget) : free_budget;
-    const size_t q_off = (sizeof(ReqDev) * d.max_requests_per_wave + 255) / 256 * 256;
     for (int i = 0; i < d.max_waves; ++i) {
         auto *w = new WaveSlot();
         w->server = s.get();
@@ -338,8 +332,7 @@ int serve_start(Ctx &ctx, const gbd_serve_config *c)
         cudaError_t e = cudaStreamCreateWithFlags(&w->stream, cudaStreamNonBlocking);
         if (e == cudaSuccess) e = cudaEventCreate(&w->ev_start);
         if (e == cudaSuccess) e = cudaEventCreate(&w->ev_stop);
-        if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void **>(&w->h_desc), sizeof(ReqDev) * d.max_requests_per_wave);
-        if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void **>(&w->d_buf), q_off + 256);
+        w->args = new WaveArgs();
         if (e != cudaSuccess) {
             ctx.server = s.release();
             serve_shutdown(ctx);
@@ -376,8 +369,7 @@ void serve_shutdown(Ctx &ctx)
         if (w->stream) cudaStreamSynchronize(w->stream);
         if (w->ev_start) cudaEventDestroy(w->ev_start);
         if (w->ev_stop) cudaEventDestroy(w->ev_stop);
-        if (w->h_desc) cudaFreeHost(w->h_desc);
-        if (w->d_buf) cudaFree(w->d_buf);
+        delete w->args;
         if (w->stream) cudaStreamDestroy(w->stream);
         delete w;
     }
@@ -433,7 +425,7 @@ int gbd_submit(gbd_ctx *ctx, const gbd_request *req, uint64_t *ticket)
     }
     ServedReq r;
     if ((rc = make_view(*vol, req->view, sp.width, sp.height, sp.fov_u, sp.fov_v, r.view))) return rc;
-    r.bytes = sizeof(ReqDev) + (sp.out_on_host ? static_cast<uint64_t>(sp.width) * sp.height * 4 : 0);
+    r.bytes = sp.out_on_host ? static_cast<uint64_t>(sp.width) * sp.height * 4 : 0;
     if (r.bytes > s.request_budget)
         return fail(GBD_ERR_BUDGET, "request needs %llu device bytes, the serving budget is %llu",
                     static_cast<unsigned long long>(r.bytes), static_cast<unsigned long long>(s.request_budget));

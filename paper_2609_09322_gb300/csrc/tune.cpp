@@ -10,6 +10,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <memory>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -67,22 +68,23 @@ int time_config(Ctx &ctx, const Volume &vol, const std::vector<ViewDev> &hv, con
 {
     const int n = static_cast<int>(hv.size());
     char *scratch = nullptr;
-    const size_t vbytes = sizeof(ViewDev) * hv.size();
-    const size_t qoff = (vbytes + 255) / 256 * 256;
-    cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&scratch), qoff + 256, st);
+    const size_t qbytes = (static_cast<size_t>(n) * sizeof(int) + 255) / 256 * 256;
+    cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&scratch), qbytes, st);
     if (e != cudaSuccess) return cuda_fail(e, "tune scratch");
-    e = cudaMemcpyAsync(scratch, hv.data(), vbytes, cudaMemcpyHostToDevice, st);
     cudaEvent_t a = nullptr, b = nullptr;
     if (e == cudaSuccess) e = cudaEventCreate(&a);
     if (e == cudaSuccess) e = cudaEventCreate(&b);
     std::vector<float> times;
+    auto args = std::make_unique<MarchArgs>();
+    const int chunks = march_chunks(n);
     for (int r = 0; r <= reps && e == cudaSuccess; ++r) {
-        MarchArgs args;
-        fill_args(args, vol, reinterpret_cast<ViewDev *>(scratch), n, spec, spec.out, nullptr,
-                  reinterpret_cast<int *>(scratch + qoff), cfg, ctx.err_word);
-        e = cudaMemsetAsync(scratch + qoff, 0, 256, st);
+        e = cudaMemsetAsync(scratch, 0, qbytes, st);
         if (e == cudaSuccess) e = cudaEventRecord(a, st);
-        if (e == cudaSuccess) e = launch_march(args, cfg, ctx.num_sms, st);
+        for (int c = 0; c < chunks && e == cudaSuccess; ++c) {
+            fill_args(*args, vol, hv.data(), n, c, spec, spec.out, nullptr, reinterpret_cast<int *>(scratch), cfg,
+                      ctx.err_word);
+            e = launch_march(*args, cfg, ctx.num_sms, st);
+        }
         if (e == cudaSuccess) e = cudaEventRecord(b, st);
         if (e == cudaSuccess) e = cudaEventSynchronize(b);
         float ms = 0.f;
