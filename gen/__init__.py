@@ -264,6 +264,44 @@ def twin_ejecta(*, n: int = 96, radius: float = 12.0, gamma: float = 2.0, theta_
     return grid, j, beta, [view], meta
 
 
+def ejectum(sign: int, *, radius: float = 8.0, gamma: float = 2.0, theta_deg: float = 45.0, c_dt: float = 1.0,
+            size: int = 64, lookback: bool = True, view_shift: float = 0.0, dtype=np.float32):
+    """One homogeneous ejectum (j' = 1), a sphere of rest-frame radius
+    ``radius`` moving along sign * z with Lorentz factor ``gamma`` (a lab-frame
+    spheroid of axial ratio 1 / gamma), stored over every epoch its observed
+    light-cone slice needs at cadence ``c_dt`` (c = 1), viewed at theta.
+
+    Returns (grid, j, beta, view, t_mid, kappa): the view is centred on the
+    ejectum at the middle epoch time t_mid and kappa = 1 - beta cos(theta) for
+    the approaching one (sign +1), 1 + beta cos(theta) for the receding one.
+    Without lookback one epoch is stored, with the ejectum at the box centre.
+    ``view_shift`` moves the view centre along y (the axis the view runs
+    parallel to) so that no pixel's ray lies in a cell-face plane."""
+    beta = math.sqrt(1.0 - 1.0 / (gamma * gamma))
+    kappa = 1.0 - sign * beta * math.cos(math.radians(theta_deg))
+    span = 2.0 * radius / kappa + 3.0 * c_dt / kappa + 4.0
+    M = int(math.ceil(span / c_dt)) + 1 if lookback else 1
+    nxy = int(math.ceil(2 * (radius + 2)))
+    zpad = radius / gamma + 2.0
+    nz = int(math.ceil(beta * (M - 1) * c_dt + 2 * zpad))
+    grid = Grid(n=(nxy, nxy, nz), n_epochs=M, t0=0.0, dt=c_dt)
+    x = grid.cell_centres(0)[None, None, :]
+    y = grid.cell_centres(1)[None, :, None]
+    z = grid.cell_centres(2)[:, None, None]
+    z0 = (zpad if sign > 0 else nz - zpad) if lookback else 0.5 * nz
+    j = np.zeros((M, nz, nxy, nxy), dtype)
+    b = np.zeros((M, nz, nxy, nxy, 3), dtype)
+    for m in range(M):
+        zc = z0 + sign * beta * m * c_dt
+        inside = (x - nxy / 2) ** 2 + (y - nxy / 2) ** 2 + ((z - zc) * gamma) ** 2 <= radius * radius
+        j[m] = inside
+        b[m, ..., 2] = np.where(inside, sign * beta, 0.0)
+    t_mid = 0.5 * (M - 1) * c_dt
+    centre = (nxy / 2, nxy / 2 + view_shift, z0 + sign * beta * t_mid)
+    v = view_from_angles(grid, theta_deg, 0.0, size=size, fov=3.2 * radius, c=1.0, beaming=True, lookback=lookback)
+    return grid, j, b, v.with_(center=centre, t_obs=t_mid), t_mid, kappa
+
+
 # --------------------------------------------------------------------------
 # Kolmogorov fields for the turbulent-jet configurations
 # --------------------------------------------------------------------------

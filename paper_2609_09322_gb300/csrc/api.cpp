@@ -285,6 +285,43 @@ int check_spec(const gbd_image_spec *s)
 
 int march_chunks(int n) { return (n + kViewsPerLaunch - 1) / kViewsPerLaunch; }
 
+// Estimated cell-samples of one view: the box-and-window chord of a 16 x 16
+// subsample of its rays, times the cells crossed per unit length.  It only
+// sizes the persistent grid's share per view, so a coarse figure will do.
+double view_work(const Volume &vol, const ViewDev &V, int width, int height)
+{
+    const int sx = std::min(width, 16), sy = std::min(height, 16);
+    double rate = 0.0;
+    for (int i = 0; i < 3; ++i) rate += static_cast<double>(V.a_hi[i]) + V.a_lo[i];
+    double cells = 0.0;
+    for (int jy = 0; jy < sy; ++jy) {
+        const int q = static_cast<int>((jy + 0.5) * height / sy);
+        for (int jx = 0; jx < sx; ++jx) {
+            const int p = static_cast<int>((jx + 0.5) * width / sx);
+            double lo = V.win_lo, hi = V.win_hi;
+            bool hit = true;
+            for (int i = 0; i < 3 && hit; ++i) {
+                const double g = static_cast<double>(V.g0[i] + p * V.gu[i] + q * V.gv[i]) * 0x1p-40;
+                if (V.inv_a[i] != 0.f) {
+                    lo = std::max(lo, -g * V.inv_a[i]);
+                    hi = std::min(hi, (vol.grid.n[i] - g) * V.inv_a[i]);
+                } else if (g < 0.0 || g >= vol.grid.n[i]) {
+                    hit = false;
+                }
+            }
+            if (hit && hi > lo) cells += (hi - lo) * rate + 1.0;
+        }
+    }
+    return cells * (static_cast<double>(width) * height) / (static_cast<double>(sx) * sy);
+}
+
+std::vector<double> view_works(const Volume &vol, const std::vector<ViewDev> &hv, int width, int height)
+{
+    std::vector<double> w(hv.size());
+    for (size_t k = 0; k < hv.size(); ++k) w[k] = view_work(vol, hv[k], width, height);
+    return w;
+}
+
 // Launch arguments of chunk c of a batch of n views: views c K .. c K + K - 1
 // (K = kViewsPerLaunch), their images and their tile counters.
 void fill_args(MarchArgs &a, const Volume &vol, const ViewDev *hv, int n, int c, const gbd_image_spec &s,
@@ -331,10 +368,11 @@ int render_direct(Ctx &ctx, const Volume &vol, const std::vector<ViewDev> &hv, c
     e = cudaMemsetAsync(queue, 0, img_off, st);
     const int chunks = march_chunks(n);
     auto a = std::make_unique<MarchArgs>();
+    const std::vector<double> work = view_works(vol, hv, spec.width, spec.height);
     for (int c = 0; c < chunks && e == cudaSuccess; ++c) {
         fill_args(*a, vol, hv.data(), n, c, spec, dev_out, spec.out_on_host ? nullptr : spec.samples, queue, cfg,
                   ctx.err_word);
-        e = launch_march(*a, cfg, ctx.num_sms, st);
+        e = launch_march(*a, cfg, ctx.num_sms, work.data() + static_cast<size_t>(c) * kViewsPerLaunch, st);
     }
     if (e == cudaSuccess && spec.out_on_host)
         e = cudaMemcpyAsync(spec.out, dev_out, pix * sizeof(float), cudaMemcpyDeviceToHost, st);
@@ -416,8 +454,10 @@ static cudaError_t chunk_params(Ctx &ctx, const Volume &vol, const GraphKey &key
     float *dev_out = spec.out_on_host ? reinterpret_cast<float *>(g.d_scratch + img_off) : spec.out;
     fill_args(a, vol, hv, key.n, c, spec, dev_out, spec.out_on_host ? nullptr : spec.samples, queue, key.cfg,
               ctx.err_word);
+    double work[kViewsPerLaunch];
+    for (int v = 0; v < a.n_views; ++v) work[v] = view_work(vol, a.views[v], spec.width, spec.height);
     KernelLaunch L;
-    cudaError_t e = plan_march(a, key.cfg, ctx.num_sms, L);
+    cudaError_t e = plan_march(a, key.cfg, ctx.num_sms, work, L);
     if (e != cudaSuccess) return e;
     std::memset(&kp, 0, sizeof(kp));
     kp.func = L.func;

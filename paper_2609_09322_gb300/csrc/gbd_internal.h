@@ -94,7 +94,7 @@ struct MarchArgs {
     int width, height;
     int packet_w, packet_h;   // packet_w * packet_h == 32
     int tiles_x, tiles_y;     // packets per image row / column
-    int blocks_per_view;      // CTAs per view (set by plan_march)
+    int cta_begin[kViewsPerLaunch + 1];  // first CTA of each view, then the total (set by plan_march)
     int persistent;           // CTAs loop over their view's tile counter
     float *out;               // n_views * width * height floats
     uint32_t *samples;        // optional, same shape
@@ -143,10 +143,11 @@ struct KernelLaunch {
 };
 
 // Kernel entry points (march.cu, pack.cu).  plan_march picks the kernel and
-// grid for a filled MarchArgs and sets its blocks_per_view; launch_march plans
-// and launches.
-cudaError_t plan_march(MarchArgs &a, const LaunchCfg &cfg, int num_sms, KernelLaunch &k);
-cudaError_t launch_march(MarchArgs &a, const LaunchCfg &cfg, int num_sms, cudaStream_t stream);
+// grid for a filled MarchArgs and sets its cta_begin; `work` (n_views
+// estimates, or NULL for equal shares) splits a persistent grid over the
+// views.  launch_march plans and launches.
+cudaError_t plan_march(MarchArgs &a, const LaunchCfg &cfg, int num_sms, const double *work, KernelLaunch &k);
+cudaError_t launch_march(MarchArgs &a, const LaunchCfg &cfg, int num_sms, const double *work, cudaStream_t stream);
 cudaError_t launch_wave(const WaveArgs &a, const LaunchCfg &cfg, cudaStream_t stream);
 
 struct PackArgs {

@@ -452,9 +452,12 @@ __device__ __forceinline__ void march_ray(const VolDev &vol, const ViewDev &V, i
 // MINB = 1 leaves the register count to the compiler; MINB = 3 asks for
 // three 256-thread CTAs per SM (at most 80 registers per thread).
 //
-// Each CTA works on one view (blockIdx.x / blocks_per_view), one packet per
-// warp: its tile directly, or, persistent, tiles pulled from the view's
-// counter until none are left.
+// Each CTA works on one view, one packet per warp: its tile directly, or,
+// persistent, tiles pulled from the view's counter until none are left.  The
+// CTAs of view v are cta_begin[v] .. cta_begin[v + 1] - 1 (persistent grids
+// give each view a share of the GPU in proportion to its estimated work); a
+// binary search over these parameter-space bounds keeps the view index
+// uniform across the CTA.
 template <int STORE, int DEPTH, int MINB, bool PAIRED>
 __global__ void __launch_bounds__(256, MINB) march_kernel(const __grid_constant__ MarchArgs a)
 {
@@ -466,8 +469,14 @@ __global__ void __launch_bounds__(256, MINB) march_kernel(const __grid_constant_
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const int wpc = blockDim.x >> 5;
-    const int vi = static_cast<int>(blockIdx.x) / a.blocks_per_view;
-    const int cb = static_cast<int>(blockIdx.x) - vi * a.blocks_per_view;
+    const int b = static_cast<int>(blockIdx.x);
+    int vi = 0, hi = a.n_views - 1;  // last view whose first CTA is <= b
+    while (vi < hi) {
+        const int mid = (vi + hi + 1) >> 1;
+        if (a.cta_begin[mid] <= b) vi = mid;
+        else hi = mid - 1;
+    }
+    const int cb = b - a.cta_begin[vi];
     const ViewDev &V = a.views[vi];
     const int tiles = a.tiles_x * a.tiles_y;
     const long long img = static_cast<long long>(vi) * a.width * a.height;
@@ -586,7 +595,7 @@ cudaError_t launch_wave(const WaveArgs &a, const LaunchCfg &cfg, cudaStream_t st
                             stream);
 }
 
-cudaError_t plan_march(MarchArgs &a, const LaunchCfg &cfg, int num_sms, KernelLaunch &L)
+cudaError_t plan_march(MarchArgs &a, const LaunchCfg &cfg, int num_sms, const double *work, KernelLaunch &L)
 {
     void *k = select_kernel(a.vol.store, cfg.depth, cfg.regcap, a.vol.paired);
     if (!k || a.n_views < 1 || a.n_views > kViewsPerLaunch) return cudaErrorInvalidValue;
@@ -598,30 +607,42 @@ cudaError_t plan_march(MarchArgs &a, const LaunchCfg &cfg, int num_sms, KernelLa
     }
     const long long tiles = static_cast<long long>(a.tiles_x) * a.tiles_y;
     const long long needed = (tiles + cfg.cta_warps - 1) / cfg.cta_warps;
-    long long per_view = needed;
+    long long total = 0;
     if (a.persistent) {
-        // enough CTAs to fill the GPU once, shared out over the views
+        // enough CTAs to fill the GPU once, shared out over the views in
+        // proportion to their estimated work (at least one CTA each)
         int per_sm = 0;
         cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, threads, smem);
         if (e != cudaSuccess) return e;
         if (per_sm < 1) per_sm = 1;
         const long long resident = static_cast<long long>(per_sm) * num_sms;
-        per_view = std::min(needed, std::max(1LL, (resident + a.n_views - 1) / a.n_views));
+        double sum = 0.0;
+        for (int v = 0; v < a.n_views; ++v) sum += work ? std::max(work[v], 0.0) : 1.0;
+        for (int v = 0; v < a.n_views; ++v) {
+            const double share = sum > 0.0 ? (work ? std::max(work[v], 0.0) : 1.0) / sum : 1.0 / a.n_views;
+            const long long c = std::min(needed, std::max(1LL, static_cast<long long>(share * resident + 0.5)));
+            a.cta_begin[v] = static_cast<int>(total);
+            total += c;
+        }
+    } else {
+        for (int v = 0; v < a.n_views; ++v) {
+            a.cta_begin[v] = static_cast<int>(total);
+            total += needed;
+        }
     }
-    const long long blocks = per_view * a.n_views;
-    if (blocks < 1 || blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
-    a.blocks_per_view = static_cast<int>(per_view);
+    if (total < 1 || total > 0x7fffffffLL) return cudaErrorInvalidValue;
+    a.cta_begin[a.n_views] = static_cast<int>(total);
     L.func = k;
-    L.grid = dim3(static_cast<unsigned>(blocks));
+    L.grid = dim3(static_cast<unsigned>(total));
     L.block = dim3(threads);
     L.smem = smem;
     return cudaSuccess;
 }
 
-cudaError_t launch_march(MarchArgs &a, const LaunchCfg &cfg, int num_sms, cudaStream_t stream)
+cudaError_t launch_march(MarchArgs &a, const LaunchCfg &cfg, int num_sms, const double *work, cudaStream_t stream)
 {
     KernelLaunch L;
-    cudaError_t e = plan_march(a, cfg, num_sms, L);
+    cudaError_t e = plan_march(a, cfg, num_sms, work, L);
     if (e != cudaSuccess) return e;
     void *params[] = {&a};
     return cudaLaunchKernel(L.func, L.grid, L.block, params, L.smem, stream);

@@ -32,6 +32,7 @@ std::mutex g_mu;                          // guards the arrays below
 void *g_scratch_addr[kMaxDevices] = {};   // device address of g_scratch, per device
 ViewDev g_host_views[kNoAllocMaxViews];   // the views, set up on the host
 MarchArgs g_args;                         // launch arguments (about 28 KB: not on the stack)
+double g_work[kViewsPerLaunch];           // per-view work estimates of one launch
 
 // Looks up the device address of the scratch array on the current device
 // (once per device; the caller holds g_mu and has made `dev` current).
@@ -85,7 +86,9 @@ extern "C" int gbd_render_batch_noalloc(gbd_ctx *ctx, gbd_volume vid, const gbd_
     const int chunks = march_chunks(n);
     for (int c = 0; c < chunks && e == cudaSuccess; ++c) {
         fill_args(g_args, *vol, g_host_views, n, c, *spec, spec->out, spec->samples, queue, cfg, ctx->err_word);
-        e = launch_march(g_args, cfg, ctx->num_sms, st);
+        for (int v = 0; v < g_args.n_views; ++v)
+            g_work[v] = view_work(*vol, g_args.views[v], spec->width, spec->height);
+        e = launch_march(g_args, cfg, ctx->num_sms, g_work, st);
     }
     if (e != cudaSuccess) return cuda_fail(e, "no-alloc batch launch");
     set_launch_count(chunks);

@@ -99,6 +99,8 @@ int check_launch(const LaunchCfg &c);
 // A batch of n views runs as march_chunks(n) launches; fill_args sets up the
 // arguments of launch c from the host view array hv.
 int march_chunks(int n);
+double view_work(const Volume &vol, const ViewDev &V, int width, int height);
+std::vector<double> view_works(const Volume &vol, const std::vector<ViewDev> &hv, int width, int height);
 void fill_args(MarchArgs &a, const Volume &vol, const ViewDev *hv, int n, int c, const gbd_image_spec &s,
                float *out, uint32_t *samples, int *queue, const LaunchCfg &cfg, int *err_word);
 bool build_layout(const int n[3], int B, int S, std::vector<int32_t> &tab, long long &epoch_stride, int morton_cells);

@@ -77,13 +77,14 @@ int time_config(Ctx &ctx, const Volume &vol, const std::vector<ViewDev> &hv, con
     std::vector<float> times;
     auto args = std::make_unique<MarchArgs>();
     const int chunks = march_chunks(n);
+    const std::vector<double> work = view_works(vol, hv, spec.width, spec.height);
     for (int r = 0; r <= reps && e == cudaSuccess; ++r) {
         e = cudaMemsetAsync(scratch, 0, qbytes, st);
         if (e == cudaSuccess) e = cudaEventRecord(a, st);
         for (int c = 0; c < chunks && e == cudaSuccess; ++c) {
             fill_args(*args, vol, hv.data(), n, c, spec, spec.out, nullptr, reinterpret_cast<int *>(scratch), cfg,
                       ctx.err_word);
-            e = launch_march(*args, cfg, ctx.num_sms, st);
+            e = launch_march(*args, cfg, ctx.num_sms, work.data() + static_cast<size_t>(c) * kViewsPerLaunch, st);
         }
         if (e == cudaSuccess) e = cudaEventRecord(b, st);
         if (e == cudaSuccess) e = cudaEventSynchronize(b);

@@ -312,7 +312,8 @@ class Context:
 
     def render_batch(self, vol: int, views, *, out=None, samples: bool = False, launch=None, stream=None):
         """Images [n][height][width] of views sharing one image geometry, in
-        one persistent launch."""
+        one call (up to 128 views per kernel launch, replayed from a cached
+        CUDA graph)."""
         import torch
         views = list(views)
         v0 = views[0]

@@ -27,33 +27,8 @@ def _paper(routine):
 
 
 def ejectum(sign, *, c_dt=1.0, size=64, lookback=True):
-    """One ejectum moving along sign * z, stored over every epoch its observed
-    light-cone slice needs.  Returns (grid, j, beta, view, t_obs_mid, kappa)
-    with kappa = 1 - beta . n_hat (n_hat towards the observer)."""
-    kappa = 1.0 - sign * BETA * math.cos(math.radians(THETA))
-    span = 2.0 * R / kappa + 3.0 * c_dt / kappa + 4.0
-    M = int(math.ceil(span / c_dt)) + 1 if lookback else 1
-    nxy = int(math.ceil(2 * (R + 2)))
-    zpad = R / GAMMA + 2.0
-    nz = int(math.ceil(BETA * (M - 1) * c_dt + 2 * zpad))
-    grid = gen.Grid(n=(nxy, nxy, nz), n_epochs=M, t0=0.0, dt=c_dt)
-    x = grid.cell_centres(0)[None, None, :]
-    y = grid.cell_centres(1)[None, :, None]
-    z = grid.cell_centres(2)[:, None, None]
-    z0 = zpad if sign > 0 else nz - zpad
-    if not lookback:
-        z0 = 0.5 * nz
-    j = np.zeros((M, nz, nxy, nxy), np.float32)
-    b = np.zeros((M, nz, nxy, nxy, 3), np.float32)
-    for m in range(M):
-        zc = z0 + sign * BETA * m * c_dt
-        inside = (x - nxy / 2) ** 2 + (y - nxy / 2) ** 2 + ((z - zc) * GAMMA) ** 2 <= R * R
-        j[m] = inside
-        b[m, ..., 2] = np.where(inside, sign * BETA, 0.0)
-    t_mid = 0.5 * (M - 1) * c_dt
-    centre = (nxy / 2, nxy / 2, z0 + sign * BETA * t_mid)
-    v = gen.view_from_angles(grid, THETA, 0.0, size=size, fov=3.2 * R, c=1.0, beaming=True, lookback=lookback)
-    return grid, j, b, v.with_(center=centre, t_obs=t_mid), t_mid, kappa
+    """One ejectum moving along sign * z (see gen.ejectum)."""
+    return gen.ejectum(sign, radius=R, gamma=GAMMA, theta_deg=THETA, c_dt=c_dt, size=size, lookback=lookback)
 
 
 def _flux(grid, j, b, v):
