@@ -163,6 +163,13 @@ typedef struct {
     int32_t persistent;          /* 1 = CTAs loop over their view's tile counter;
                                     0 = one packet per warp, one launch wave    */
     int32_t regcap;              /* 1 = kernel built for at most 80 registers/thread */
+    int32_t region;              /* batches: 0 = march every ray whole; 16, 32, 64
+                                    or 128 = region schedule: march all views' rays
+                                    region by region (edge^3 cells, while the region
+                                    is in L2), then add each ray's region sums in
+                                    order.  Images agree with the whole-ray march to
+                                    FP32 rounding (a few 1e-6), not bitwise.  Not
+                                    used with sample counts; depth 1 or 2.           */
 } gbd_launch;
 
 /* Description of a resident volume. */

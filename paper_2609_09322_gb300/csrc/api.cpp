@@ -252,7 +252,7 @@ VolDev vol_dev(const Volume &v)
 
 LaunchCfg resolve_launch(const gbd_launch *l)
 {
-    LaunchCfg c{8, 4, 8, 2, 1, 0};
+    LaunchCfg c{8, 4, 8, 2, 1, 0, 0};
     if (l) {
         if (l->packet_w > 0) c.packet_w = l->packet_w;
         if (l->packet_h > 0) c.packet_h = l->packet_h;
@@ -260,6 +260,7 @@ LaunchCfg resolve_launch(const gbd_launch *l)
         if (l->depth > 0) c.depth = l->depth;
         c.persistent = l->persistent != 0;
         c.regcap = l->regcap != 0;
+        c.region = l->region;
     }
     return c;
 }
@@ -271,6 +272,9 @@ int check_launch(const LaunchCfg &c)
     if (c.cta_warps != 1 && c.cta_warps != 2 && c.cta_warps != 4 && c.cta_warps != 8)
         return fail(GBD_ERR_INVALID, "launch: cta_warps must be 1, 2, 4 or 8");
     if (c.depth != 1 && c.depth != 2 && c.depth != 4) return fail(GBD_ERR_INVALID, "launch: depth must be 1, 2 or 4");
+    if (c.region != 0 && c.region != 16 && c.region != 32 && c.region != 64 && c.region != 128)
+        return fail(GBD_ERR_INVALID, "launch: region must be 0, 16, 32, 64 or 128");
+    if (c.region != 0 && c.depth > 2) return fail(GBD_ERR_INVALID, "launch: the region schedule takes depth 1 or 2");
     return GBD_OK;
 }
 
@@ -350,15 +354,155 @@ void fill_args(MarchArgs &a, const Volume &vol, const ViewDev *hv, int n, int c,
 // Bytes of the per-view tile counters of a batch, rounded up to 256.
 static size_t queue_bytes(int n) { return (static_cast<size_t>(n) * sizeof(int) + 255) / 256 * 256; }
 
+// ------------------------------------------------------------ region schedule
+// Pixel coordinates of the march frame for view V: the first two rows of the
+// inverse of the map (p, q, s) -> g0 + p gu + q gv + s a.
+RegionProj region_proj(const ViewDev &V)
+{
+    double m[3][3], g0[3];
+    for (int i = 0; i < 3; ++i) {
+        m[i][0] = static_cast<double>(V.gu[i]) * 0x1p-40;
+        m[i][1] = static_cast<double>(V.gv[i]) * 0x1p-40;
+        m[i][2] = static_cast<double>(V.a_hi[i]) + V.a_lo[i];
+        g0[i] = static_cast<double>(V.g0[i]) * 0x1p-40;
+    }
+    const double c00 = m[1][1] * m[2][2] - m[1][2] * m[2][1];
+    const double c01 = m[1][2] * m[2][0] - m[1][0] * m[2][2];
+    const double c02 = m[1][0] * m[2][1] - m[1][1] * m[2][0];
+    const double det = m[0][0] * c00 + m[0][1] * c01 + m[0][2] * c02;
+    // rows 0 and 1 of the inverse: (adjugate transposed) / det
+    const double r0[3] = {c00 / det, (m[0][2] * m[2][1] - m[0][1] * m[2][2]) / det,
+                          (m[0][1] * m[1][2] - m[0][2] * m[1][1]) / det};
+    const double r1[3] = {c01 / det, (m[0][0] * m[2][2] - m[0][2] * m[2][0]) / det,
+                          (m[0][2] * m[1][0] - m[0][0] * m[1][2]) / det};
+    RegionProj P;
+    double p0 = 0.0, q0 = 0.0;
+    for (int i = 0; i < 3; ++i) {
+        P.ip[i] = static_cast<float>(r0[i]);
+        P.iq[i] = static_cast<float>(r1[i]);
+        p0 -= r0[i] * g0[i];
+        q0 -= r1[i] * g0[i];
+    }
+    P.p0 = static_cast<float>(p0);
+    P.q0 = static_cast<float>(q0);
+    return P;
+}
+
+// Regions per axis and partial slots of the region schedule; 0 if it does not
+// apply (no region edge set, sample counts wanted, or too many regions).
+int region_slots(const Volume &vol, const LaunchCfg &cfg, const gbd_image_spec &spec, int nreg[3])
+{
+    if (cfg.region <= 0 || spec.samples) return 0;
+    long long regions = 1;
+    int slots = 0;
+    for (int i = 0; i < 3; ++i) {
+        nreg[i] = (vol.grid.n[i] + cfg.region - 1) / cfg.region;
+        regions *= nreg[i];
+        slots += nreg[i];
+    }
+    if (regions > 65535) return 0;
+    return slots - 2;
+}
+
+// CTAs one view needs per region: the projection of a region's box covers at
+// most this many packets (a pixel of margin on each side, plus alignment).
+static int region_ctas(const RegionProj &P, int region, const LaunchCfg &cfg)
+{
+    double hp = 0.0, hq = 0.0;
+    for (int i = 0; i < 3; ++i) {
+        hp += std::fabs(static_cast<double>(P.ip[i])) * 0.5 * region;
+        hq += std::fabs(static_cast<double>(P.iq[i])) * 0.5 * region;
+    }
+    const long long ntx = static_cast<long long>((2.0 * hp + 5.0) / cfg.packet_w) + 2;
+    const long long nty = static_cast<long long>((2.0 * hq + 5.0) / cfg.packet_h) + 2;
+    return static_cast<int>((ntx * nty + cfg.cta_warps - 1) / cfg.cta_warps);
+}
+
+// Enqueues a region-schedule batch on st: clear the partial slots, march the
+// regions (one launch per kViewsPerRegionLaunch views, each over all regions),
+// then add up the slots into dev_out.  partial holds slots * n * W * H floats.
+cudaError_t enqueue_regions(Ctx &ctx, const Volume &vol, const std::vector<ViewDev> &hv, const gbd_image_spec &spec,
+                            const LaunchCfg &cfg, float *dev_out, float *partial, cudaStream_t st, int *launches)
+{
+    int nreg[3];
+    const int slots = region_slots(vol, cfg, spec, nreg);
+    const int n = static_cast<int>(hv.size());
+    const long long pix = static_cast<long long>(spec.width) * spec.height;
+    const long long slot_stride = pix * n;
+    cudaError_t e = cudaMemsetAsync(partial, 0, sizeof(float) * static_cast<size_t>(slot_stride) * slots, st);
+    auto a = std::make_unique<RegionArgs>();
+    *launches = 0;
+    for (int first = 0; first < n && e == cudaSuccess; first += kViewsPerRegionLaunch) {
+        const int cnt = std::min(kViewsPerRegionLaunch, n - first);
+        std::memset(a.get(), 0, sizeof(RegionArgs));
+        a->vol = vol_dev(vol);
+        a->n_views = cnt;
+        a->width = spec.width;
+        a->height = spec.height;
+        a->packet_w = cfg.packet_w;
+        a->packet_h = cfg.packet_h;
+        a->region = cfg.region;
+        for (int i = 0; i < 3; ++i) a->nreg[i] = nreg[i];
+        a->partial = partial + first * pix;
+        a->slot_stride = slot_stride;
+        a->error_word = ctx.err_word;
+        long long total = 0;
+        for (int v = 0; v < cnt; ++v) {
+            a->views[v] = hv[first + v];
+            a->proj[v] = region_proj(a->views[v]);
+            a->cta_begin[v] = static_cast<int>(total);
+            total += region_ctas(a->proj[v], cfg.region, cfg);
+        }
+        if (total > 0x7fffffffLL) return cudaErrorInvalidValue;
+        a->cta_begin[cnt] = static_cast<int>(total);
+        e = launch_region(*a, cfg, st);
+        ++*launches;
+    }
+    auto r = std::make_unique<ReduceArgs>();
+    for (int first = 0; first < n && e == cudaSuccess; first += kViewsPerRegionLaunch) {
+        const int cnt = std::min(kViewsPerRegionLaunch, n - first);
+        std::memset(r.get(), 0, sizeof(ReduceArgs));
+        r->out = dev_out + first * pix;
+        r->partial = partial + first * pix;
+        r->slot_stride = slot_stride;
+        r->pix_per_view = pix;
+        r->n_views = cnt;
+        r->n_slots = slots;
+        for (int v = 0; v < cnt; ++v) r->prefactor[v] = hv[first + v].prefactor;
+        e = launch_reduce(*r, st);
+        ++*launches;
+    }
+    return e;
+}
+
 // Renders n views whose records are already set up on the host, without a
-// cached graph: stream-ordered scratch for the tile counters (and the image
-// when it goes to host memory), one launch per kViewsPerLaunch views.
+// cached graph: stream-ordered scratch for the tile counters or partial slots
+// (and the image when it goes to host memory).
 int render_direct(Ctx &ctx, const Volume &vol, const std::vector<ViewDev> &hv, const gbd_image_spec &spec,
                   const LaunchCfg &cfg, cudaStream_t st)
 {
     const int n = static_cast<int>(hv.size());
     const size_t pix = static_cast<size_t>(spec.width) * spec.height * n;
     char *scratch = nullptr;
+    int nreg[3];
+    const int slots = region_slots(vol, cfg, spec, nreg);
+    if (slots > 0) {
+        const size_t pbytes = sizeof(float) * pix * static_cast<size_t>(slots);
+        const size_t total = pbytes + (spec.out_on_host ? pix * sizeof(float) : 0);
+        cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&scratch), total, st);
+        if (e != cudaSuccess) return cuda_fail(e, "region scratch");
+        float *partial = reinterpret_cast<float *>(scratch);
+        float *dev_out = spec.out_on_host ? reinterpret_cast<float *>(scratch + pbytes) : spec.out;
+        int launches = 0;
+        e = enqueue_regions(ctx, vol, hv, spec, cfg, dev_out, partial, st, &launches);
+        if (e == cudaSuccess && spec.out_on_host)
+            e = cudaMemcpyAsync(spec.out, dev_out, pix * sizeof(float), cudaMemcpyDeviceToHost, st);
+        cudaError_t ef = cudaFreeAsync(scratch, st);
+        if (e != cudaSuccess) return cuda_fail(e, "region render");
+        if (ef != cudaSuccess) return cuda_fail(ef, "region scratch free");
+        set_launch_count(launches);
+        return GBD_OK;
+    }
     const size_t img_off = queue_bytes(n);
     const size_t total = img_off + (spec.out_on_host ? pix * sizeof(float) : 0);
     cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&scratch), total, st);
@@ -404,6 +548,7 @@ struct GraphKey {
 struct GraphEntry {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
+    int region_launches = 0;     // region schedule: kernels per replay (captured; rebuilt for new views)
     std::vector<cudaGraphNode_t> knodes;
     std::vector<ViewDev> views;  // the views the kernel nodes hold
     char *d_scratch = nullptr;   // tile counters (+ image when out_on_host)
@@ -469,9 +614,40 @@ static cudaError_t chunk_params(Ctx &ctx, const Volume &vol, const GraphKey &key
     return cudaSuccess;
 }
 
+// Region schedule: the batch is captured from enqueue_regions.
+static int build_region_graph(Ctx &ctx, const Volume &vol, const GraphKey &key, const gbd_image_spec &spec,
+                              const std::vector<ViewDev> &hv, int slots, GraphEntry &g)
+{
+    const size_t pix = static_cast<size_t>(spec.width) * spec.height * key.n;
+    const size_t pbytes = sizeof(float) * pix * static_cast<size_t>(slots);
+    const size_t total = pbytes + (spec.out_on_host ? pix * sizeof(float) : 0);
+    cudaError_t e = cudaMalloc(reinterpret_cast<void **>(&g.d_scratch), total);
+    if (e != cudaSuccess) return cuda_fail(e, "region batch scratch");
+    e = cudaEventCreateWithFlags(&g.done, cudaEventDisableTiming);
+    if (e != cudaSuccess) return cuda_fail(e, "batch event");
+    float *partial = reinterpret_cast<float *>(g.d_scratch);
+    float *dev_out = spec.out_on_host ? reinterpret_cast<float *>(g.d_scratch + pbytes) : spec.out;
+    cudaStream_t cap = ctx.capture_stream;
+    e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return cuda_fail(e, "begin capture");
+    cudaError_t e2 = enqueue_regions(ctx, vol, hv, spec, key.cfg, dev_out, partial, cap, &g.region_launches);
+    if (e2 == cudaSuccess && spec.out_on_host)
+        e2 = cudaMemcpyAsync(spec.out, dev_out, pix * sizeof(float), cudaMemcpyDeviceToHost, cap);
+    e = cudaStreamEndCapture(cap, &g.graph);
+    if (e2 != cudaSuccess) return cuda_fail(e2, "capture region batch");
+    if (e != cudaSuccess) return cuda_fail(e, "end capture");
+    e = cudaGraphInstantiate(&g.exec, g.graph, 0);
+    if (e != cudaSuccess) return cuda_fail(e, "instantiate region batch graph");
+    g.views = hv;
+    return GBD_OK;
+}
+
 static int build_graph(Ctx &ctx, const Volume &vol, const GraphKey &key, const gbd_image_spec &spec,
                        const std::vector<ViewDev> &hv, GraphEntry &g)
 {
+    int nreg[3];
+    const int slots = region_slots(vol, key.cfg, spec, nreg);
+    if (slots > 0) return build_region_graph(ctx, vol, key, spec, hv, slots, g);
     const int n = key.n;
     const size_t img_off = queue_bytes(n);
     const size_t pix = static_cast<size_t>(spec.width) * spec.height * n;
@@ -550,6 +726,20 @@ int render_graph(Ctx &ctx, const Volume &vol, gbd_volume vid, const std::vector<
             return rc;
         }
         slot = std::move(g);
+    } else if (std::memcmp(slot->views.data(), hv.data(), vbytes) != 0 && slot->region_launches > 0) {
+        // region schedule: capture the batch again for the new views
+        if (slot->launched) {
+            cudaError_t e = cudaEventSynchronize(slot->done);
+            if (e != cudaSuccess) return cuda_fail(e, "wait for previous batch");
+        }
+        auto g = std::make_unique<GraphEntry>();
+        int rc = build_graph(ctx, vol, key, spec, hv, *g);
+        if (rc != GBD_OK) {
+            gc.entries.erase(key);
+            gc.last_use.erase(key);
+            return rc;
+        }
+        slot = std::move(g);
     } else if (std::memcmp(slot->views.data(), hv.data(), vbytes) != 0) {
         // Parameter updates apply to later launches only; a launch in flight
         // keeps the views it started with.
@@ -568,7 +758,7 @@ int render_graph(Ctx &ctx, const Volume &vol, gbd_volume vid, const std::vector<
     e = cudaEventRecord(slot->done, st);
     if (e != cudaSuccess) return cuda_fail(e, "graph event");
     slot->launched = true;
-    set_launch_count(static_cast<int>(slot->knodes.size()));
+    set_launch_count(slot->region_launches > 0 ? slot->region_launches : static_cast<int>(slot->knodes.size()));
     return GBD_OK;
 }
 

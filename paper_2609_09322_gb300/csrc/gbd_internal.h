@@ -104,6 +104,48 @@ struct MarchArgs {
 };
 static_assert(sizeof(MarchArgs) <= 32764, "march launch arguments exceed the kernel parameter limit");
 
+// Region schedule.  A batch of many views over a large volume marches every
+// ray region by region: region r (an edge^3 block of cells) is marched for all
+// views' rays that cross it while its records sit in L2, and each ray's sum
+// over the region goes to partial slot s(r), the sum of r's region coordinates
+// in the march frame, which grows by one from region to region along a ray.
+// A reduction then adds each ray's slots in order.
+constexpr int kViewsPerRegionLaunch = 96;
+
+// Pixel coordinates of a point g of a view's march frame: p = ip . g + p0,
+// q = iq . g + q0 (the first two rows of the inverse of [gu gv a]).
+struct RegionProj {
+    float ip[3], iq[3];
+    float p0, q0;
+};
+
+struct RegionArgs {
+    VolDev vol;
+    int n_views;              // views in this launch, 1 .. kViewsPerRegionLaunch
+    int width, height;
+    int packet_w, packet_h;
+    int region;               // region edge in cells
+    int nreg[3];              // regions per axis
+    float *partial;           // slot s of view v of this launch at partial + s * slot_stride + v * width * height
+    long long slot_stride;    // floats per slot
+    int *error_word;
+    int cta_begin[kViewsPerRegionLaunch + 1];  // CTAs of each view in one region (blockIdx.x)
+    RegionProj proj[kViewsPerRegionLaunch];
+    ViewDev views[kViewsPerRegionLaunch];
+};
+static_assert(sizeof(RegionArgs) <= 32764, "region launch arguments exceed the kernel parameter limit");
+
+// out[v][pixel] = prefactor[v] * (sum over slots of partial, in slot order).
+struct ReduceArgs {
+    float *out;               // this launch's first image
+    const float *partial;     // slot 0 of this launch's first image
+    long long slot_stride;    // floats per slot
+    long long pix_per_view;
+    int n_views;
+    int n_slots;
+    float prefactor[kViewsPerRegionLaunch];
+};
+
 // One request of a served wave: its own volume, view, image and outputs.
 struct ReqDev {
     VolDev vol;
@@ -132,7 +174,7 @@ static_assert(sizeof(WaveArgs) <= 32764, "wave launch arguments exceed the kerne
 
 // Launch configuration after defaults have been applied.
 struct LaunchCfg {
-    int packet_w, packet_h, cta_warps, depth, persistent, regcap;
+    int packet_w, packet_h, cta_warps, depth, persistent, regcap, region;
 };
 
 // A planned kernel launch.
@@ -149,6 +191,10 @@ struct KernelLaunch {
 cudaError_t plan_march(MarchArgs &a, const LaunchCfg &cfg, int num_sms, const double *work, KernelLaunch &k);
 cudaError_t launch_march(MarchArgs &a, const LaunchCfg &cfg, int num_sms, const double *work, cudaStream_t stream);
 cudaError_t launch_wave(const WaveArgs &a, const LaunchCfg &cfg, cudaStream_t stream);
+// Region schedule: the caller has filled everything but the grid, which
+// launch_region derives from cta_begin and the region counts.
+cudaError_t launch_region(const RegionArgs &a, const LaunchCfg &cfg, cudaStream_t stream);
+cudaError_t launch_reduce(const ReduceArgs &a, cudaStream_t stream);
 
 struct PackArgs {
     const void *j;            // one epoch, [nz][ny][nx]

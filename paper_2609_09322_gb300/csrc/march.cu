@@ -204,12 +204,39 @@ __device__ __forceinline__ void step_axis(AxisState &A, float inv_a, long long d
     A.pn = tab_at<SMEM>(tab, A.cur + 4u);
 }
 
-// Marches the ray of pixel (p, q) of one image and stores its value (and,
-// if cnt_img is set, its cell-sample count).  out_img points at the image;
-// tab at the volume's march tables (shared memory when SMEM).
-template <int STORE, int DEPTH, bool PAIRED, bool SMEM>
-__device__ __forceinline__ void march_ray(const VolDev &vol, const ViewDev &V, int p, int q, int width, int height,
-                                          float *out_img, uint32_t *cnt_img, int *err_word,
+// The box a ray is marched through, in the march frame (mirrored axes
+// mirrored), and where its table terms start: the whole grid for a direct
+// render, one region of it for the region schedule.  Along axis i the cells
+// lo[i] .. hi[i] - 1 have their terms at byte offsets cur0[i], cur0[i] + 4, ...
+// followed by two sentinels.
+struct RayBox {
+    int lo[3], hi[3];
+    uint32_t cur0[3];
+};
+
+// The whole grid as seen by view V, with the volume's own march tables.
+__device__ __forceinline__ RayBox grid_box(const VolDev &vol, const ViewDev &V)
+{
+    RayBox B;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        const bool mirrored = (V.flags & (kFlagMirror0 << i)) != 0u;
+        B.lo[i] = 0;
+        B.hi[i] = vol.n[i];
+        B.cur0[i] = 4u * static_cast<uint32_t>(march_table_base(vol.n, i) + (mirrored ? vol.n[i] + 2 : 0));
+    }
+    return B;
+}
+
+// Marches the ray of pixel (p, q) of one image through box B.  Direct
+// (PARTIAL false): stores the pixel value (Eq. 19, with the prefactor) and,
+// if cnt_img is set, its cell-sample count.  PARTIAL: adds the ray's sum over
+// the box, without the prefactor, to out_img[pixel] if the ray sampled at
+// least one cell there (one region per slot and ray, so the add lands on
+// zero).  tab points at the march tables (shared memory when SMEM).
+template <int STORE, int DEPTH, bool PAIRED, bool SMEM, bool PARTIAL = false>
+__device__ __forceinline__ void march_ray(const VolDev &vol, const ViewDev &V, const RayBox &B, int p, int q,
+                                          int width, int height, float *out_img, uint32_t *cnt_img, int *err_word,
                                           const int32_t *__restrict__ tab)
 {
     using Rec = Record<STORE>;
@@ -233,9 +260,10 @@ __device__ __forceinline__ void march_ray(const VolDev &vol, const ViewDev &V, i
     for (int i = 0; i < 3; ++i) {
         if (V.inv_a[i] != 0.f) {
             const float gf = fix_to_float(g0[i], kInv2p40);
-            s_in_e = fmaxf(s_in_e, -gf * V.inv_a[i]);
-            s_out_e = fminf(s_out_e, (static_cast<float>(vol.n[i]) - gf) * V.inv_a[i]);
-        } else if (g0[i] < 0 || g0[i] >= (static_cast<long long>(vol.n[i]) << 40)) {
+            s_in_e = fmaxf(s_in_e, (static_cast<float>(B.lo[i]) - gf) * V.inv_a[i]);
+            s_out_e = fminf(s_out_e, (static_cast<float>(B.hi[i]) - gf) * V.inv_a[i]);
+        } else if (g0[i] < (static_cast<long long>(B.lo[i]) << 40) ||
+                   g0[i] >= (static_cast<long long>(B.hi[i]) << 40)) {
             alive = false;  // parallel to this axis and outside the box along it
         }
     }
@@ -259,7 +287,7 @@ __device__ __forceinline__ void march_ray(const VolDev &vol, const ViewDev &V, i
         const bool moving = V.inv_a[i] != 0.f;
         const long long ga = moving ? g0[i] + dd_mul_fix(sa, V.a_hi[i], V.a_lo[i], kTwo40) : g0[i];
         int k = static_cast<int>(ga >> 40);
-        k = min(max(k, 0), vol.n[i] - 1);
+        k = min(max(k, B.lo[i]), B.hi[i] - 1);
         const float o = fix_to_float(ga - (static_cast<long long>(k) << 40), kInv2p40);
         AxisState &A = ax[i];
         A.nkf = 1.0f;
@@ -276,8 +304,7 @@ __device__ __forceinline__ void march_ray(const VolDev &vol, const ViewDev &V, i
             A.sn = 3.0e38f;      // never the nearest face ...
             A.un = LLONG_MIN / 2;  // ... and ends the ray if it ever were
         }
-        const bool mirrored = (V.flags & (kFlagMirror0 << i)) != 0u;
-        A.cur = 4u * static_cast<uint32_t>(march_table_base(vol.n, i) + (mirrored ? vol.n[i] + 2 : 0) + k);
+        A.cur = B.cur0[i] + 4u * static_cast<uint32_t>(k - B.lo[i]);
         A.o = 0;
         A.pn = 0;
         if (alive) {
@@ -285,7 +312,7 @@ __device__ __forceinline__ void march_ray(const VolDev &vol, const ViewDev &V, i
             A.pn = tab_at<SMEM>(tab, A.cur + 4u);
         }
 #ifdef GBD_CHECKED
-        kc[i] = mirrored ? vol.n[i] - 1 - k : k;
+        kc[i] = (V.flags & (kFlagMirror0 << i)) ? vol.n[i] - 1 - k : k;
 #endif
     }
     const float ia0 = V.inv_a[0], ia1 = V.inv_a[1], ia2 = V.inv_a[2];
@@ -304,7 +331,7 @@ __device__ __forceinline__ void march_ray(const VolDev &vol, const ViewDev &V, i
     // the one before.  Each step moves one table cursor up, and a sentinel
     // stops the ray at the box face, so the loop is bounded by the grid.
     if (alive) {
-        for (int guard = vol.n[0] + vol.n[1] + vol.n[2] + 4; guard > 0; --guard) {
+        for (int guard = B.hi[0] + B.hi[1] + B.hi[2] + 4; guard > 0; --guard) {
             const bool x0 = ax[0].sn <= ax[1].sn && ax[0].sn <= ax[2].sn;
             const bool x1 = !x0 && ax[1].sn <= ax[2].sn;
             const float s_exit = x0 ? ax[0].sn : (x1 ? ax[1].sn : ax[2].sn);
@@ -444,8 +471,12 @@ __device__ __forceinline__ void march_ray(const VolDev &vol, const ViewDev &V, i
 
     if (in_image) {
         const long long pix = static_cast<long long>(q) * width + p;
-        out_img[pix] = V.prefactor * acc;
-        if (cnt_img) cnt_img[pix] = count;
+        if (PARTIAL) {
+            if (count > 0u) atomicAdd(out_img + pix, acc);
+        } else {
+            out_img[pix] = V.prefactor * acc;
+            if (cnt_img) cnt_img[pix] = count;
+        }
     }
 }
 
@@ -478,6 +509,7 @@ __global__ void __launch_bounds__(256, MINB) march_kernel(const __grid_constant_
     }
     const int cb = b - a.cta_begin[vi];
     const ViewDev &V = a.views[vi];
+    const RayBox box = grid_box(a.vol, V);
     const int tiles = a.tiles_x * a.tiles_y;
     const long long img = static_cast<long long>(vi) * a.width * a.height;
     float *out = a.out + img;
@@ -494,7 +526,7 @@ __global__ void __launch_bounds__(256, MINB) march_kernel(const __grid_constant_
         const int ty = tile / a.tiles_x;
         const int p = tx * a.packet_w + lane % a.packet_w;
         const int q = ty * a.packet_h + lane / a.packet_w;
-        march_ray<STORE, DEPTH, PAIRED, true>(a.vol, V, p, q, a.width, a.height, out, cnt, a.error_word, s_tab);
+        march_ray<STORE, DEPTH, PAIRED, true>(a.vol, V, box, p, q, a.width, a.height, out, cnt, a.error_word, s_tab);
         if (!a.persistent) break;
     }
 }
@@ -526,20 +558,110 @@ __global__ void __launch_bounds__(256, MINB) wave_kernel(const __grid_constant__
     const int p = tx * a.packet_w + lane % a.packet_w;
     const int q = ty * a.packet_h + lane / a.packet_w;
     const int32_t *tab = R.vol.mtab;
+    const RayBox box = grid_box(R.vol, R.view);
     if (R.vol.store == GBD_STORE_F32) {
         if (R.vol.paired)
-            march_ray<GBD_STORE_F32, DEPTH, true, false>(R.vol, R.view, p, q, R.width, R.height, R.out, R.samples,
+            march_ray<GBD_STORE_F32, DEPTH, true, false>(R.vol, R.view, box, p, q, R.width, R.height, R.out, R.samples,
                                                          a.error_word, tab);
         else
-            march_ray<GBD_STORE_F32, DEPTH, false, false>(R.vol, R.view, p, q, R.width, R.height, R.out, R.samples,
+            march_ray<GBD_STORE_F32, DEPTH, false, false>(R.vol, R.view, box, p, q, R.width, R.height, R.out, R.samples,
                                                           a.error_word, tab);
     } else {
         if (R.vol.paired)
-            march_ray<GBD_STORE_BF16_F16U, DEPTH, true, false>(R.vol, R.view, p, q, R.width, R.height, R.out,
+            march_ray<GBD_STORE_BF16_F16U, DEPTH, true, false>(R.vol, R.view, box, p, q, R.width, R.height, R.out,
                                                                R.samples, a.error_word, tab);
         else
-            march_ray<GBD_STORE_BF16_F16U, DEPTH, false, false>(R.vol, R.view, p, q, R.width, R.height, R.out,
+            march_ray<GBD_STORE_BF16_F16U, DEPTH, false, false>(R.vol, R.view, box, p, q, R.width, R.height, R.out,
                                                                 R.samples, a.error_word, tab);
+    }
+}
+
+// Region schedule (RegionArgs): CTA (x, y) marches rays of one view through
+// region y.  The region's table terms along each axis (forward or reversed,
+// as the view needs), followed by two sentinels, are staged in shared memory;
+// the view's pixels whose rays can cross the region are those inside the
+// projection of the region's box, and the CTA's warps take packets of that
+// rectangle.  Each ray adds its region sum to its partial slot.
+template <int STORE, int DEPTH, int MINB, bool PAIRED>
+__global__ void __launch_bounds__(256, MINB) region_kernel(const __grid_constant__ RegionArgs a)
+{
+    extern __shared__ int32_t s_tab[];
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int wpc = blockDim.x >> 5;
+    const int b = static_cast<int>(blockIdx.x);
+    int vi = 0, hi = a.n_views - 1;  // last view whose first CTA is <= b
+    while (vi < hi) {
+        const int mid = (vi + hi + 1) >> 1;
+        if (a.cta_begin[mid] <= b) vi = mid;
+        else hi = mid - 1;
+    }
+    const int cb = b - a.cta_begin[vi];
+    const ViewDev &V = a.views[vi];
+    const RegionProj &P = a.proj[vi];
+    const int r = static_cast<int>(blockIdx.y);
+    const int rr[3] = {r % a.nreg[0], (r / a.nreg[0]) % a.nreg[1], r / (a.nreg[0] * a.nreg[1])};
+    RayBox B;
+    int slot = 0;
+    float pc = P.p0, qc = P.q0, hp = 0.f, hq = 0.f;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        const int n = a.vol.n[i];
+        const int olo = rr[i] * a.region;
+        const int ohi = min(olo + a.region, n);
+        const bool mirrored = (V.flags & (kFlagMirror0 << i)) != 0u;
+        B.lo[i] = mirrored ? n - ohi : olo;
+        B.hi[i] = mirrored ? n - olo : ohi;
+        B.cur0[i] = 4u * static_cast<uint32_t>(i * (a.region + 2));
+        slot += mirrored ? a.nreg[i] - 1 - rr[i] : rr[i];
+        const float c = 0.5f * static_cast<float>(B.lo[i] + B.hi[i]);
+        const float h = 0.5f * static_cast<float>(B.hi[i] - B.lo[i]);
+        pc = fmaf(P.ip[i], c, pc);
+        qc = fmaf(P.iq[i], c, qc);
+        hp = fmaf(fabsf(P.ip[i]), h, hp);
+        hq = fmaf(fabsf(P.iq[i]), h, hq);
+    }
+    for (int i = 0; i < 3; ++i) {
+        const bool mirrored = (V.flags & (kFlagMirror0 << i)) != 0u;
+        const int len = B.hi[i] - B.lo[i];
+        const int src = march_table_base(a.vol.n, i) + (mirrored ? a.vol.n[i] + 2 : 0) + B.lo[i];
+        for (int j = threadIdx.x; j < len + 2; j += blockDim.x)
+            s_tab[i * (a.region + 2) + j] = j < len ? a.vol.mtab[src + j] : kTabSentinel;
+    }
+    __syncthreads();
+    // pixels whose centres project into the region's box, with a pixel of margin
+    const int p_lo = max(static_cast<int>(floorf(pc - hp)) - 1, 0);
+    const int p_hi = min(static_cast<int>(floorf(pc + hp)) + 1, a.width - 1);
+    const int q_lo = max(static_cast<int>(floorf(qc - hq)) - 1, 0);
+    const int q_hi = min(static_cast<int>(floorf(qc + hq)) + 1, a.height - 1);
+    if (p_hi < p_lo || q_hi < q_lo) return;
+    const int tx0 = p_lo / a.packet_w, ty0 = q_lo / a.packet_h;
+    const int ntx = p_hi / a.packet_w - tx0 + 1;
+    const int nty = q_hi / a.packet_h - ty0 + 1;
+    const int tile = cb * wpc + warp;
+    if (tile >= ntx * nty) return;
+    const int p = (tx0 + tile % ntx) * a.packet_w + lane % a.packet_w;
+    const int q = (ty0 + tile / ntx) * a.packet_h + lane / a.packet_w;
+    float *out = a.partial + static_cast<long long>(slot) * a.slot_stride +
+                 static_cast<long long>(vi) * a.width * a.height;
+    march_ray<STORE, DEPTH, PAIRED, true, true>(a.vol, V, B, p, q, a.width, a.height, out, nullptr, a.error_word,
+                                                s_tab);
+}
+
+// out = prefactor * (partial slots summed in slot order, compensated).
+__global__ void __launch_bounds__(256) reduce_kernel(const __grid_constant__ ReduceArgs a)
+{
+    const long long n = a.pix_per_view * a.n_views;
+    for (long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
+         i += static_cast<long long>(gridDim.x) * blockDim.x) {
+        float acc = 0.f, comp = 0.f;
+        for (int s = 0; s < a.n_slots; ++s) {
+            const float y = a.partial[static_cast<long long>(s) * a.slot_stride + i] - comp;
+            const float t = acc + y;
+            comp = (t - acc) - y;
+            acc = t;
+        }
+        a.out[i] = a.prefactor[static_cast<int>(i / a.pix_per_view)] * acc;
     }
 }
 
@@ -576,6 +698,33 @@ void *select_kernel(int store, int depth, int capped, int paired)
     return nullptr;
 }
 
+template <int STORE, int MINB, bool PAIRED>
+void *select_region_depth(int depth)
+{
+    switch (depth) {
+    case 1: return reinterpret_cast<void *>(&region_kernel<STORE, 1, MINB, PAIRED>);
+    case 2: return reinterpret_cast<void *>(&region_kernel<STORE, 2, MINB, PAIRED>);
+    default: return nullptr;
+    }
+}
+
+void *select_region(int store, int depth, int capped, int paired)
+{
+    if (store == GBD_STORE_F32) {
+        if (paired) return capped ? select_region_depth<GBD_STORE_F32, 3, true>(depth)
+                                  : select_region_depth<GBD_STORE_F32, 1, true>(depth);
+        return capped ? select_region_depth<GBD_STORE_F32, 3, false>(depth)
+                      : select_region_depth<GBD_STORE_F32, 1, false>(depth);
+    }
+    if (store == GBD_STORE_BF16_F16U) {
+        if (paired) return capped ? select_region_depth<GBD_STORE_BF16_F16U, 3, true>(depth)
+                                  : select_region_depth<GBD_STORE_BF16_F16U, 1, true>(depth);
+        return capped ? select_region_depth<GBD_STORE_BF16_F16U, 3, false>(depth)
+                      : select_region_depth<GBD_STORE_BF16_F16U, 1, false>(depth);
+    }
+    return nullptr;
+}
+
 void *select_wave(int depth, int capped)
 {
     if (depth == 1) return capped ? reinterpret_cast<void *>(&wave_kernel<1, 3>) : reinterpret_cast<void *>(&wave_kernel<1, 1>);
@@ -593,6 +742,29 @@ cudaError_t launch_wave(const WaveArgs &a, const LaunchCfg &cfg, cudaStream_t st
     void *params[] = {const_cast<WaveArgs *>(&a)};
     return cudaLaunchKernel(k, dim3(static_cast<unsigned>(a.total_ctas)), dim3(32 * cfg.cta_warps), params, 0,
                             stream);
+}
+
+cudaError_t launch_region(const RegionArgs &a, const LaunchCfg &cfg, cudaStream_t stream)
+{
+    void *k = select_region(a.vol.store, cfg.depth, cfg.regcap, a.vol.paired);
+    if (!k || a.n_views < 1 || a.n_views > kViewsPerRegionLaunch) return cudaErrorInvalidValue;
+    const long long regions = static_cast<long long>(a.nreg[0]) * a.nreg[1] * a.nreg[2];
+    const int ctas = a.cta_begin[a.n_views];
+    if (ctas < 1 || regions < 1 || regions > 65535) return cudaErrorInvalidValue;
+    const int smem = static_cast<int>(sizeof(int32_t)) * 3 * (a.region + 2);
+    void *params[] = {const_cast<RegionArgs *>(&a)};
+    return cudaLaunchKernel(k, dim3(static_cast<unsigned>(ctas), static_cast<unsigned>(regions)),
+                            dim3(32 * cfg.cta_warps), params, smem, stream);
+}
+
+cudaError_t launch_reduce(const ReduceArgs &a, cudaStream_t stream)
+{
+    const long long n = a.pix_per_view * a.n_views;
+    if (n < 1) return cudaSuccess;
+    const long long blocks = std::min<long long>((n + 255) / 256, 152LL * 16);
+    void *params[] = {const_cast<ReduceArgs *>(&a)};
+    return cudaLaunchKernel(reinterpret_cast<void *>(&reduce_kernel), dim3(static_cast<unsigned>(blocks)), dim3(256),
+                            params, 0, stream);
 }
 
 cudaError_t plan_march(MarchArgs &a, const LaunchCfg &cfg, int num_sms, const double *work, KernelLaunch &L)

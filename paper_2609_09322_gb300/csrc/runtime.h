@@ -100,6 +100,10 @@ int check_launch(const LaunchCfg &c);
 // arguments of launch c from the host view array hv.
 int march_chunks(int n);
 double view_work(const Volume &vol, const ViewDev &V, int width, int height);
+// Region schedule (see RegionArgs): slots per ray, 0 when it does not apply.
+int region_slots(const Volume &vol, const LaunchCfg &cfg, const gbd_image_spec &spec, int nreg[3]);
+cudaError_t enqueue_regions(Ctx &ctx, const Volume &vol, const std::vector<ViewDev> &hv, const gbd_image_spec &spec,
+                            const LaunchCfg &cfg, float *dev_out, float *partial, cudaStream_t st, int *launches);
 std::vector<double> view_works(const Volume &vol, const std::vector<ViewDev> &hv, int width, int height);
 void fill_args(MarchArgs &a, const Volume &vol, const ViewDev *hv, int n, int c, const gbd_image_spec &s,
                float *out, uint32_t *samples, int *queue, const LaunchCfg &cfg, int *err_word);

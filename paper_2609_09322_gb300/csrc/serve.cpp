@@ -70,7 +70,7 @@ struct Server {
     Ctx *ctx = nullptr;
     int device = 0;
     gbd_serve_config cfg{};
-    LaunchCfg launch{8, 4, 8, 1, 1, 0};
+    LaunchCfg launch{8, 4, 8, 1, 1, 0, 0};
     uint64_t request_budget = 0;
     std::mutex mu;
     std::condition_variable cv;       // wakes the scheduler
@@ -319,6 +319,7 @@ int serve_start(Ctx &ctx, const gbd_serve_config *c)
     if (!c) lc.depth = 1;
     if (lc.depth > 2) lc.depth = 2;
     lc.persistent = 1;
+    lc.region = 0;  // waves march whole rays
     int rc = check_launch(lc);
     if (rc) return rc;
     s->launch = lc;

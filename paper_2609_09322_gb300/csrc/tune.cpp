@@ -56,8 +56,9 @@ void append_cache_file(const TuneKey &k, const TuneEntry &e)
     std::lock_guard<std::mutex> lock(g_file_mu);
     FILE *f = std::fopen(path, "a");
     if (!f) return;
-    std::fprintf(f, "%s -> %d %d %d %d %d %d %d %d %.6f\n", key_text(k).c_str(), e.cfg.packet_w, e.cfg.packet_h,
-                 e.cfg.cta_warps, e.cfg.depth, e.cfg.persistent, e.cfg.regcap, e.brick, e.super_brick, e.ms);
+    std::fprintf(f, "%s -> %d %d %d %d %d %d %d %d %d %.6f\n", key_text(k).c_str(), e.cfg.packet_w, e.cfg.packet_h,
+                 e.cfg.cta_warps, e.cfg.depth, e.cfg.persistent, e.cfg.regcap, e.cfg.region, e.brick, e.super_brick,
+                 e.ms);
     std::fclose(f);
 }
 
@@ -68,7 +69,11 @@ int time_config(Ctx &ctx, const Volume &vol, const std::vector<ViewDev> &hv, con
 {
     const int n = static_cast<int>(hv.size());
     char *scratch = nullptr;
-    const size_t qbytes = (static_cast<size_t>(n) * sizeof(int) + 255) / 256 * 256;
+    int nreg[3];
+    const int slots = region_slots(vol, cfg, spec, nreg);
+    const size_t pix = static_cast<size_t>(spec.width) * spec.height * n;
+    const size_t qbytes = slots > 0 ? sizeof(float) * pix * static_cast<size_t>(slots)
+                                    : (static_cast<size_t>(n) * sizeof(int) + 255) / 256 * 256;
     cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&scratch), qbytes, st);
     if (e != cudaSuccess) return cuda_fail(e, "tune scratch");
     cudaEvent_t a = nullptr, b = nullptr;
@@ -79,9 +84,12 @@ int time_config(Ctx &ctx, const Volume &vol, const std::vector<ViewDev> &hv, con
     const int chunks = march_chunks(n);
     const std::vector<double> work = view_works(vol, hv, spec.width, spec.height);
     for (int r = 0; r <= reps && e == cudaSuccess; ++r) {
-        e = cudaMemsetAsync(scratch, 0, qbytes, st);
+        e = slots > 0 ? cudaSuccess : cudaMemsetAsync(scratch, 0, qbytes, st);
         if (e == cudaSuccess) e = cudaEventRecord(a, st);
-        for (int c = 0; c < chunks && e == cudaSuccess; ++c) {
+        int launches = 0;
+        if (slots > 0 && e == cudaSuccess)
+            e = enqueue_regions(ctx, vol, hv, spec, cfg, spec.out, reinterpret_cast<float *>(scratch), st, &launches);
+        for (int c = 0; c < chunks && e == cudaSuccess && slots == 0; ++c) {
             fill_args(*args, vol, hv.data(), n, c, spec, spec.out, nullptr, reinterpret_cast<int *>(scratch), cfg,
                       ctx.err_word);
             e = launch_march(*args, cfg, ctx.num_sms, work.data() + static_cast<size_t>(c) * kViewsPerLaunch, st);
@@ -193,10 +201,10 @@ void load_tune_file(Ctx &ctx)
         TuneKey k;
         std::memset(&k, 0, sizeof(k));
         TuneEntry e;
-        if (std::sscanf(line, "%d %d %d %d %d %d %d %d %d -> %d %d %d %d %d %d %d %d %f", &k.n[0], &k.n[1],
+        if (std::sscanf(line, "%d %d %d %d %d %d %d %d %d -> %d %d %d %d %d %d %d %d %d %f", &k.n[0], &k.n[1],
                         &k.n[2], &k.M, &k.store, &k.width, &k.height, &k.n_views, &k.lookback, &e.cfg.packet_w,
                         &e.cfg.packet_h, &e.cfg.cta_warps, &e.cfg.depth, &e.cfg.persistent, &e.cfg.regcap,
-                        &e.brick, &e.super_brick, &e.ms) == 18 &&
+                        &e.cfg.region, &e.brick, &e.super_brick, &e.ms) == 19 &&
             check_launch(e.cfg) == GBD_OK)
             ctx.tuned[k] = e;  // later lines win
     }
@@ -247,10 +255,12 @@ int gbd_tune(gbd_ctx *ctx, gbd_volume vid, const gbd_view *views, int32_t n, con
     const bool verbose = std::getenv("GBD_TUNE_VERBOSE") != nullptr;
     auto report = [&](const LaunchCfg &c, float ms, int B, int S) {
         if (verbose)
-            std::fprintf(stderr, "gbd_tune: packet %2dx%-2d warps %d depth %d persistent %d regcap %d layout %d/%d: %.4f ms\n",
-                         c.packet_w, c.packet_h, c.cta_warps, c.depth, c.persistent, c.regcap, B, S, ms);
+            std::fprintf(stderr,
+                         "gbd_tune: packet %2dx%-2d warps %d depth %d persistent %d regcap %d region %d layout %d/%d: "
+                         "%.4f ms\n",
+                         c.packet_w, c.packet_h, c.cta_warps, c.depth, c.persistent, c.regcap, c.region, B, S, ms);
     };
-    LaunchCfg best{8, 4, 8, 2, 1, 0};
+    LaunchCfg best{8, 4, 8, 2, 1, 0, 0};
     float best_ms = 0.f;
     int tried = 0;
     if ((rc = time_config(*ctx, *vol, hv, *spec, best, st, 3, best_ms))) return rc;
@@ -264,7 +274,7 @@ int gbd_tune(gbd_ctx *ctx, gbd_volume vid, const gbd_view *views, int32_t n, con
             for (const auto &pk : packets)
                 for (int w : warps)
                     for (int d : depths) {
-                        LaunchCfg c{pk[0], pk[1], w, d, 1, cap};
+                        LaunchCfg c{pk[0], pk[1], w, d, 1, cap, 0};
                         float ms = 0.f;
                         if ((rc = time_config(*ctx, *vol, hv, *spec, c, st, 3, ms))) return rc;
                         report(c, ms, vol->brick, vol->super_brick);
@@ -274,7 +284,7 @@ int gbd_tune(gbd_ctx *ctx, gbd_volume vid, const gbd_view *views, int32_t n, con
                             best = c;
                         }
                     }
-        LaunchCfg flat{8, 4, 8, 2, 0, 0};
+        LaunchCfg flat{8, 4, 8, 2, 0, 0, 0};
         float ms = 0.f;
         if ((rc = time_config(*ctx, *vol, hv, *spec, flat, st, 3, ms))) return rc;
         report(flat, ms, vol->brick, vol->super_brick);
@@ -282,6 +292,29 @@ int gbd_tune(gbd_ctx *ctx, gbd_volume vid, const gbd_view *views, int32_t n, con
         if (ms < best_ms) {
             best_ms = ms;
             best = flat;
+        }
+        // region schedule, for batches of many views
+        if (n >= 8) {
+            const int regions[2] = {32, 64};
+            const int rpackets[2][2] = {{8, 4}, {4, 8}};
+            const int rwarps[2] = {4, 8};
+            int nreg[3];
+            for (int reg : regions)
+                for (int cap = 0; cap < 2; ++cap)
+                    for (const auto &pk : rpackets)
+                        for (int w : rwarps)
+                            for (int d = 1; d <= 2; ++d) {
+                                LaunchCfg c{pk[0], pk[1], w, d, 0, cap, reg};
+                                if (region_slots(*vol, c, *spec, nreg) == 0) continue;
+                                float rms = 0.f;
+                                if ((rc = time_config(*ctx, *vol, hv, *spec, c, st, 3, rms))) return rc;
+                                report(c, rms, vol->brick, vol->super_brick);
+                                ++tried;
+                                if (rms < best_ms) {
+                                    best_ms = rms;
+                                    best = c;
+                                }
+                            }
         }
     }
     if (what & GBD_TUNE_LAYOUT) {
@@ -328,6 +361,7 @@ int gbd_tune(gbd_ctx *ctx, gbd_volume vid, const gbd_view *views, int32_t n, con
     out->launch.depth = best.depth;
     out->launch.persistent = best.persistent;
     out->launch.regcap = best.regcap;
+    out->launch.region = best.region;
     out->brick = vol->brick;
     out->super_brick = vol->super_brick;
     out->paired = vol->paired;

@@ -57,7 +57,8 @@ class ImageSpec(ctypes.Structure):
 
 class Launch(ctypes.Structure):
     _fields_ = [("packet_w", ctypes.c_int32), ("packet_h", ctypes.c_int32), ("cta_warps", ctypes.c_int32),
-                ("depth", ctypes.c_int32), ("persistent", ctypes.c_int32), ("regcap", ctypes.c_int32)]
+                ("depth", ctypes.c_int32), ("persistent", ctypes.c_int32), ("regcap", ctypes.c_int32),
+                ("region", ctypes.c_int32)]
 
 
 class TuneResult(ctypes.Structure):
@@ -186,6 +187,7 @@ def _launch(launch) -> ctypes.POINTER(Launch) | None:
     lw.depth = launch.get("depth", 0)
     lw.persistent = int(launch.get("persistent", 1))
     lw.regcap = int(launch.get("regcap", 0))
+    lw.region = int(launch.get("region", 0))
     return ctypes.pointer(lw)
 
 
@@ -375,7 +377,8 @@ class Context:
                                            _stream_handle(stream), ctypes.byref(res)))
         lw = res.launch
         return dict(packet=(lw.packet_w, lw.packet_h), cta_warps=lw.cta_warps, depth=lw.depth,
-                    persistent=lw.persistent, regcap=lw.regcap, brick=res.brick, super_brick=res.super_brick,
+                    persistent=lw.persistent, regcap=lw.regcap, region=lw.region, brick=res.brick,
+                    super_brick=res.super_brick,
                     paired=res.paired, morton_cells=res.morton_cells, ms=res.ms, candidates=res.candidates)
 
     def relayout(self, vol: int, brick: int, super_brick: int, paired: bool = False, morton_cells: bool = False):

@@ -3,7 +3,8 @@ benchmark times, on sampled pixels the oracle computes one by one.
 
   time-delay   256^3 x 16 FP32, 18 views of 512^2 (the benchmark workload)
   precision    512^3 x 8 stored as BF16 j' + FP16 four-velocity, 1024^2
-  batched      384^3 x 32 FP32, 256 views of 256^2 in one launch
+  batched      384^3 x 32 FP32, 256 views of 256^2 in one launch, marched
+               whole ray by whole ray and region by region
 
 The FP32 workloads are held to the 1e-5 per-pixel bound (the oracle reads
 the same float32 fields); the BF16/FP16 one to 1e-2 per pixel and 1e-3 in
@@ -90,4 +91,28 @@ def test_batched_full_size(ctx):
         pix = _sample(rng, imgs[k], 300)
         ref = oracle.render_pixels(grid, j, beta, views[k], pix)
         assert_parity(imgs[k][pix[:, 1], pix[:, 0]], ref, what=f"batched view {k}")
+    ctx.unload(vol)
+
+
+def test_batched_full_size_region_schedule(ctx):
+    """The batched-views workload in the region schedule (32^3 regions): the
+    sampled pixels against the oracle, and every pixel against the whole-ray
+    march of the same batch."""
+    grid, jd, bd, views = gen.config_batched_device(device="cuda:0")
+    vol = ctx.load_snapshots(grid, jd, bd, brick=4, super_brick=2, paired=True)
+    launch = {"packet": (8, 4), "cta_warps": 8, "depth": 2, "persistent": 0, "regcap": 1, "region": 32}
+    imgs = ctx.render_batch(vol, views, launch=launch)
+    whole = ctx.render_batch(vol, views, launch=BENCH_LAUNCH)
+    torch.cuda.synchronize()
+    imgs, whole = imgs.cpu().numpy(), whole.cpu().numpy()
+    j, beta = jd.cpu().numpy(), bd.cpu().numpy()
+    del jd, bd
+    torch.cuda.empty_cache()
+    for k in range(0, len(views), 17):
+        assert_parity(imgs[k], whole[k], rel=2e-5, what=f"region vs whole ray, view {k}")
+    rng = np.random.default_rng(14)
+    for k in (3, 100, 201):
+        pix = _sample(rng, imgs[k], 300)
+        ref = oracle.render_pixels(grid, j, beta, views[k], pix)
+        assert_parity(imgs[k][pix[:, 1], pix[:, 0]], ref, what=f"region schedule view {k}")
     ctx.unload(vol)
