@@ -138,6 +138,18 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------ peaks
+def reduce_over_ranks(value: float, op: str, device: str) -> float:
+    """``value`` combined over all ranks of the default process group ("max" or
+    "sum"); the value itself on a single process."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
+    return float(t.item())
+
+
 def measured_peak_hbm():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -251,9 +263,7 @@ def run_gpu(args, rank: int, world: int):
     total_ms = ev[0].elapsed_time(ev[-1])
     if world > 1:
         dist.barrier()
-        t = torch.tensor([total_ms], device=f"cuda:{dev}")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+        total_ms = reduce_over_ranks(total_ms, "max", f"cuda:{dev}")
     ms_per_step = total_ms / args.steps
     step()  # one more, untimed, to read how many march kernels a step launches
     stream.synchronize()
@@ -402,6 +412,13 @@ def run_serving(args, rank: int, world: int):
     sat = run_phase(None, 0, total)
     r_sat = sat["requests_per_s"]
     points = [run_phase(f * r_sat, 0, total) for f in (0.5, 0.8, 0.95)]
+    # replicas: every rank serves its own stream; rates add up over the ranks
+    # and latencies are the worst rank's
+    for ph in [sat] + points:
+        for k in ("requests_per_s", "gcell_samples_per_s", "completed"):
+            ph[k] = round(reduce_over_ranks(ph[k], "sum", device), 3)
+        for k in ("p50_ms", "p99_ms", "max_ms"):
+            ph[k] = round(reduce_over_ranks(ph[k], "max", device), 3)
     top = points[-1]
     result = {
         "metric": METRIC, "value": top["gcell_samples_per_s"], "unit": UNIT, "n_gpus": world,
@@ -509,9 +526,14 @@ def main():
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
+        import torch
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
     if args.workload == "serving":
+        result = run_serving(args, rank, world)
         if rank == 0:
-            print(json.dumps(run_serving(args, rank, world)), flush=True)
+            print(json.dumps(result), flush=True)
+        if world > 1:
+            dist.destroy_process_group()
         return
     result, clocks, wl = run_gpu(args, rank, world)
     result["clocks"] = clocks

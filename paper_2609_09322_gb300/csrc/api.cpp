@@ -418,9 +418,32 @@ static int region_ctas(const RegionProj &P, int region, const LaunchCfg &cfg)
     return static_cast<int>((ntx * nty + cfg.cta_warps - 1) / cfg.cta_warps);
 }
 
+// Order in which the region schedule launches a batch's views: by the Morton
+// code of the direction s_hat (10 bits per component).  Views of nearby
+// directions see a region at nearby depths, hence nearby snapshots, so the CTAs
+// that run side by side on a region read the same few snapshots of it.
+static std::vector<int> direction_order(const std::vector<ViewDev> &hv)
+{
+    std::vector<std::pair<uint64_t, int>> key(hv.size());
+    for (size_t k = 0; k < hv.size(); ++k) {
+        uint64_t code = 0;
+        for (int i = 0; i < 3; ++i) {
+            const double s = static_cast<double>(hv[k].sh_hi[i]) + hv[k].sh_lo[i];
+            const uint64_t c = static_cast<uint64_t>(std::min(1023.0, std::max(0.0, (s + 1.0) * 511.5)));
+            for (int bit = 0; bit < 10; ++bit) code |= ((c >> bit) & 1u) << (3 * bit + i);
+        }
+        key[k] = {code, static_cast<int>(k)};
+    }
+    std::stable_sort(key.begin(), key.end());
+    std::vector<int> order(hv.size());
+    for (size_t k = 0; k < hv.size(); ++k) order[k] = key[k].second;
+    return order;
+}
+
 // Enqueues a region-schedule batch on st: clear the partial slots, march the
-// regions (one launch per kViewsPerRegionLaunch views, each over all regions),
-// then add up the slots into dev_out.  partial holds slots * n * W * H floats.
+// regions (one launch per kViewsPerRegionLaunch views in direction order, each
+// over all regions), then add up the slots into dev_out.  partial holds
+// slots * n * W * H floats.
 cudaError_t enqueue_regions(Ctx &ctx, const Volume &vol, const std::vector<ViewDev> &hv, const gbd_image_spec &spec,
                             const LaunchCfg &cfg, float *dev_out, float *partial, cudaStream_t st, int *launches)
 {
@@ -431,6 +454,7 @@ cudaError_t enqueue_regions(Ctx &ctx, const Volume &vol, const std::vector<ViewD
     const long long slot_stride = pix * n;
     cudaError_t e = cudaMemsetAsync(partial, 0, sizeof(float) * static_cast<size_t>(slot_stride) * slots, st);
     auto a = std::make_unique<RegionArgs>();
+    const std::vector<int> order = direction_order(hv);
     *launches = 0;
     for (int first = 0; first < n && e == cudaSuccess; first += kViewsPerRegionLaunch) {
         const int cnt = std::min(kViewsPerRegionLaunch, n - first);
@@ -443,12 +467,13 @@ cudaError_t enqueue_regions(Ctx &ctx, const Volume &vol, const std::vector<ViewD
         a->packet_h = cfg.packet_h;
         a->region = cfg.region;
         for (int i = 0; i < 3; ++i) a->nreg[i] = nreg[i];
-        a->partial = partial + first * pix;
+        a->partial = partial;
         a->slot_stride = slot_stride;
         a->error_word = ctx.err_word;
         long long total = 0;
         for (int v = 0; v < cnt; ++v) {
-            a->views[v] = hv[first + v];
+            a->batch_view[v] = order[first + v];
+            a->views[v] = hv[order[first + v]];
             a->proj[v] = region_proj(a->views[v]);
             a->cta_begin[v] = static_cast<int>(total);
             total += region_ctas(a->proj[v], cfg.region, cfg);

@@ -126,10 +126,11 @@ struct RegionArgs {
     int packet_w, packet_h;
     int region;               // region edge in cells
     int nreg[3];              // regions per axis
-    float *partial;           // slot s of view v of this launch at partial + s * slot_stride + v * width * height
+    float *partial;           // slot s of batch view b at partial + s * slot_stride + b * width * height
     long long slot_stride;    // floats per slot
     int *error_word;
     int cta_begin[kViewsPerRegionLaunch + 1];  // CTAs of each view in one region (blockIdx.x)
+    int batch_view[kViewsPerRegionLaunch];     // the view's index in the batch
     RegionProj proj[kViewsPerRegionLaunch];
     ViewDev views[kViewsPerRegionLaunch];
 };

@@ -643,7 +643,7 @@ __global__ void __launch_bounds__(256, MINB) region_kernel(const __grid_constant
     const int p = (tx0 + tile % ntx) * a.packet_w + lane % a.packet_w;
     const int q = (ty0 + tile / ntx) * a.packet_h + lane / a.packet_w;
     float *out = a.partial + static_cast<long long>(slot) * a.slot_stride +
-                 static_cast<long long>(vi) * a.width * a.height;
+                 static_cast<long long>(a.batch_view[vi]) * a.width * a.height;
     march_ray<STORE, DEPTH, PAIRED, true, true>(a.vol, V, B, p, q, a.width, a.height, out, nullptr, a.error_word,
                                                 s_tab);
 }
