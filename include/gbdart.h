@@ -250,6 +250,50 @@ int gbd_render_batch(gbd_ctx *ctx, gbd_volume vol, const gbd_view *views, int32_
 int gbd_render_batch_noalloc(gbd_ctx *ctx, gbd_volume vol, const gbd_view *views, int32_t n,
                              const gbd_image_spec *spec, const gbd_launch *launch, void *stream);
 
+/* Out-of-core rendering (the paper's partial sub-region renders and
+ * selective snapshot loading, Secs. 5.2 and 6.2).  Renders n views of a
+ * volume that stays in host memory: the volume is cut into slabs of `slab`
+ * cells along z (0: 64); each slab is uploaded, with flexload only the
+ * snapshots that some view's rays inside the slab can reach in time, packed
+ * on the device as a volume of its own and marched for every view, its sums
+ * added to the images.  Two slab buffers alternate, so a slab's upload and
+ * packing on the context's load stream overlap the previous slab's march on
+ * `stream`.
+ *  - fields: host arrays (pinned for overlapped copies; on_device must be 0),
+ *    laid out as for gbd_load_snapshots; store, brick and super_brick apply to
+ *    the slabs;
+ *  - spec->out (and samples) must be device memory; they are overwritten;
+ *  - the images agree with gbd_render_batch of the whole volume to float32
+ *    rounding (each slab restarts the ray's anchor; within 2e-5 relative);
+ *  - device memory: two slab buffers (records of the slab's snapshots, its
+ *    tables, one snapshot of raw fields), checked against the budget
+ *    (GBD_ERR_BUDGET);
+ *  - the call returns when the images are complete; info receives the slabs
+ *    marched and the bytes uploaded against the bytes of the whole series. */
+typedef struct {
+    int32_t slab;              /* in: cells per slab along z (0 = 64)                 */
+    int32_t flexload;          /* in: 1 = upload only the snapshots a slab can reach  */
+    int32_t slabs;             /* out: slabs marched (slabs no ray reaches are skipped) */
+    uint64_t bytes_uploaded;   /* out: raw field bytes copied to the device           */
+    uint64_t bytes_total;      /* out: raw field bytes of the whole series            */
+} gbd_stream_info;
+int gbd_render_streamed(gbd_ctx *ctx, const gbd_grid *grid, const gbd_fields *fields, const gbd_view *views,
+                        int32_t n, const gbd_image_spec *spec, const gbd_launch *launch, gbd_stream_info *info,
+                        void *stream);
+
+/* Labelled mode (the paper's second input form, Sec. 4): a scene made of
+ * several sub-domains of locally homogeneous resolution -- for instance the
+ * levels of a mesh-refined simulation -- each loaded as its own volume with
+ * its own grid (origin, cell size, dimensions, snapshot times).  A pixel's
+ * intensity is the sum over the sub-domains of its ray's sum through each
+ * (Eq. 19 over the union of their cells); the sub-domains are marched in the
+ * order given and added into spec->out (device memory, overwritten).  The
+ * boxes of the sub-domains must not overlap (they may touch), otherwise
+ * GBD_ERR_INVALID: where a refined level covers a coarser one, the coarser
+ * one is to be cut into boxes around it. */
+int gbd_render_labelled(gbd_ctx *ctx, const gbd_volume *vols, int32_t n_vols, const gbd_view *views, int32_t n,
+                        const gbd_image_spec *spec, const gbd_launch *launch, void *stream);
+
 /* Number of kernels the last successful render call of this thread
  * launched (graph replays count their kernels). */
 int32_t gbd_last_launch_count(void);

@@ -19,7 +19,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
-SOURCES = ["api.cpp", "runtime.cpp", "serve.cpp", "tune.cpp", "march.cu", "pack.cu", "noalloc.cu"]
+SOURCES = ["api.cpp", "runtime.cpp", "serve.cpp", "tune.cpp", "stream.cpp", "march.cu", "pack.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -121,6 +121,27 @@ bool build_layout(const int n[3], int B, int S, std::vector<int32_t> &tab, long 
     return true;
 }
 
+// Validates a grid and the description of its fields (not their values).
+int check_grid_fields(const gbd_grid &g, const gbd_fields &f)
+{
+    for (int i = 0; i < 3; ++i) {
+        if (g.n[i] < 1 || g.n[i] > kMaxAxis) return fail(GBD_ERR_INVALID, "grid: n[%d] must be in [1, %d]", i, kMaxAxis);
+        if (!(g.dx[i] > 0.0) || !std::isfinite(g.dx[i]) || !std::isfinite(g.origin[i]))
+            return fail(GBD_ERR_INVALID, "grid: dx must be positive and origin finite");
+    }
+    if (g.n_epochs < 1 || g.n_epochs > 1000000) return fail(GBD_ERR_INVALID, "grid: n_epochs must be >= 1");
+    if (!(g.dt > 0.0) || !std::isfinite(g.dt) || !std::isfinite(g.t0))
+        return fail(GBD_ERR_INVALID, "grid: dt must be positive and t0 finite");
+    if (!f.j || !f.vel) return fail(GBD_ERR_INVALID, "fields: NULL array");
+    if (f.dtype_in != GBD_IN_F64 && f.dtype_in != GBD_IN_F32) return fail(GBD_ERR_INVALID, "fields: bad dtype_in");
+    if (f.store != GBD_STORE_F32 && f.store != GBD_STORE_BF16_F16U) return fail(GBD_ERR_INVALID, "fields: bad store");
+    const int B = f.brick ? f.brick : 8;
+    const int S = f.super_brick ? f.super_brick : 4;
+    if (B != 1 && B != 2 && B != 4 && B != 8) return fail(GBD_ERR_INVALID, "fields: brick must be 1, 2, 4 or 8");
+    if (S != 1 && S != 2 && S != 4) return fail(GBD_ERR_INVALID, "fields: super_brick must be 1, 2 or 4");
+    return GBD_OK;
+}
+
 // ------------------------------------------------------------------ views
 static bool finite3(const double v[3]) { return std::isfinite(v[0]) && std::isfinite(v[1]) && std::isfinite(v[2]); }
 
@@ -893,21 +914,10 @@ int gbd_load_snapshots(gbd_ctx *ctx, const gbd_grid *grid, const gbd_fields *f, 
     if (!ctx || !grid || !f || !out) return fail(GBD_ERR_INVALID, "NULL argument");
     *out = 0;
     const gbd_grid &g = *grid;
-    for (int i = 0; i < 3; ++i) {
-        if (g.n[i] < 1 || g.n[i] > kMaxAxis) return fail(GBD_ERR_INVALID, "grid: n[%d] must be in [1, %d]", i, kMaxAxis);
-        if (!(g.dx[i] > 0.0) || !std::isfinite(g.dx[i]) || !std::isfinite(g.origin[i]))
-            return fail(GBD_ERR_INVALID, "grid: dx must be positive and origin finite");
-    }
-    if (g.n_epochs < 1 || g.n_epochs > 1000000) return fail(GBD_ERR_INVALID, "grid: n_epochs must be >= 1");
-    if (!(g.dt > 0.0) || !std::isfinite(g.dt) || !std::isfinite(g.t0))
-        return fail(GBD_ERR_INVALID, "grid: dt must be positive and t0 finite");
-    if (!f->j || !f->vel) return fail(GBD_ERR_INVALID, "fields: NULL array");
-    if (f->dtype_in != GBD_IN_F64 && f->dtype_in != GBD_IN_F32) return fail(GBD_ERR_INVALID, "fields: bad dtype_in");
-    if (f->store != GBD_STORE_F32 && f->store != GBD_STORE_BF16_F16U) return fail(GBD_ERR_INVALID, "fields: bad store");
-    int B = f->brick ? f->brick : 8;
-    int S = f->super_brick ? f->super_brick : 4;
-    if (B != 1 && B != 2 && B != 4 && B != 8) return fail(GBD_ERR_INVALID, "fields: brick must be 1, 2, 4 or 8");
-    if (S != 1 && S != 2 && S != 4) return fail(GBD_ERR_INVALID, "fields: super_brick must be 1, 2 or 4");
+    int rc = check_grid_fields(g, *f);
+    if (rc) return rc;
+    const int B = f->brick ? f->brick : 8;
+    const int S = f->super_brick ? f->super_brick : 4;
 
     std::lock_guard<std::mutex> lock(ctx->mu);
     DeviceGuard guard(ctx->device);

@@ -96,6 +96,7 @@ struct MarchArgs {
     int tiles_x, tiles_y;     // packets per image row / column
     int cta_begin[kViewsPerLaunch + 1];  // first CTA of each view, then the total (set by plan_march)
     int persistent;           // CTAs loop over their view's tile counter
+    int accumulate;           // add to out (and samples) instead of storing
     float *out;               // n_views * width * height floats
     uint32_t *samples;        // optional, same shape
     int *queue;               // persistent mode: one tile counter per view (zeroed before launch)

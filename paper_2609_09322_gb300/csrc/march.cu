@@ -116,6 +116,8 @@ struct Record<GBD_STORE_BF16_F16U> {
     // D = 1 / (Gamma + u.s_hat).  When u.s_hat < 0 (motion towards the
     // observer) the denominator cancels, so the same D is evaluated as
     // (Gamma + |u.s_hat|) / (1 + |u|^2 - (u.s_hat)^2), which has no cancellation.
+    // s_hat enters rounded to float: its rounding (6e-8) is far below the
+    // float16 resolution of u (5e-4 relative), unlike in the float32 record.
     static __device__ __forceinline__ float boosted(const T r, const BoostConsts &c)
     {
         const float j = __uint_as_float(r.x << 16);
@@ -123,8 +125,7 @@ struct Record<GBD_STORE_BF16_F16U> {
         const float ux = __half2float(__ushort_as_half(static_cast<unsigned short>(r.x >> 16)));
         const float uy = __half2float(__ushort_as_half(static_cast<unsigned short>(r.y & 0xffffu)));
         const float uz = __half2float(__ushort_as_half(static_cast<unsigned short>(r.y >> 16)));
-        float us = fmaf(ux, c.shx, fmaf(uy, c.shy, uz * c.shz));
-        us += fmaf(ux, c.slx, fmaf(uy, c.sly, uz * c.slz));
+        const float us = fmaf(ux, c.shx, fmaf(uy, c.shy, uz * c.shz));
         const float uu = fmaf(ux, ux, fmaf(uy, uy, uz * uz));
         const float gp = sqrt_approx(1.0f + uu) + fabsf(us);
         const float perp = 1.0f + fmaf(-us, us, uu);
@@ -230,14 +231,16 @@ __device__ __forceinline__ RayBox grid_box(const VolDev &vol, const ViewDev &V)
 
 // Marches the ray of pixel (p, q) of one image through box B.  Direct
 // (PARTIAL false): stores the pixel value (Eq. 19, with the prefactor) and,
-// if cnt_img is set, its cell-sample count.  PARTIAL: adds the ray's sum over
+// if cnt_img is set, its cell-sample count, or adds them to what is there
+// when `accumulate` is set (one thread owns each pixel, so the adds of
+// successive launches land in launch order).  PARTIAL: adds the ray's sum over
 // the box, without the prefactor, to out_img[pixel] if the ray sampled at
 // least one cell there (one region per slot and ray, so the add lands on
 // zero).  tab points at the march tables (shared memory when SMEM).
 template <int STORE, int DEPTH, bool PAIRED, bool SMEM, bool PARTIAL = false>
 __device__ __forceinline__ void march_ray(const VolDev &vol, const ViewDev &V, const RayBox &B, int p, int q,
                                           int width, int height, float *out_img, uint32_t *cnt_img, int *err_word,
-                                          const int32_t *__restrict__ tab)
+                                          const int32_t *__restrict__ tab, bool accumulate = false)
 {
     using Rec = Record<STORE>;
     const bool in_image = (p < width) && (q < height);
@@ -473,6 +476,9 @@ __device__ __forceinline__ void march_ray(const VolDev &vol, const ViewDev &V, c
         const long long pix = static_cast<long long>(q) * width + p;
         if (PARTIAL) {
             if (count > 0u) atomicAdd(out_img + pix, acc);
+        } else if (accumulate) {
+            out_img[pix] += V.prefactor * acc;
+            if (cnt_img) cnt_img[pix] += count;
         } else {
             out_img[pix] = V.prefactor * acc;
             if (cnt_img) cnt_img[pix] = count;
@@ -526,7 +532,8 @@ __global__ void __launch_bounds__(256, MINB) march_kernel(const __grid_constant_
         const int ty = tile / a.tiles_x;
         const int p = tx * a.packet_w + lane % a.packet_w;
         const int q = ty * a.packet_h + lane / a.packet_w;
-        march_ray<STORE, DEPTH, PAIRED, true>(a.vol, V, box, p, q, a.width, a.height, out, cnt, a.error_word, s_tab);
+        march_ray<STORE, DEPTH, PAIRED, true>(a.vol, V, box, p, q, a.width, a.height, out, cnt, a.error_word, s_tab,
+                                              a.accumulate != 0);
         if (!a.persistent) break;
     }
 }

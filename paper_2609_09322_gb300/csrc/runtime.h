@@ -23,7 +23,7 @@ struct Volume {
     int paired = 0;                  // blocks of side-by-side snapshot pairs
     int morton_cells = 0;            // Morton order of the cells inside a brick
     void *rec = nullptr;             // records, block after block
-    int32_t *axis_off = nullptr;     // per-axis offset tables (n_x + n_y + n_z)
+    int32_t *axis_off = nullptr;     // per-axis offset tables (n_x + n_y + n_z), then the march tables
     long long epoch_stride = 0;      // records per block (epoch, or epoch pair)
     uint64_t bytes = 0;              // device bytes charged to the budget
     std::atomic<int> pinned_by_requests{0};  // queued or running serving requests using it
@@ -93,6 +93,8 @@ void reset_fault_counters();
 
 // View and launch helpers (api.cpp).
 int make_view(const Volume &vol, const gbd_view &v, int width, int height, double fov_u, double fov_v, ViewDev &out);
+int check_grid_fields(const gbd_grid &g, const gbd_fields &f);
+int check_spec(const gbd_image_spec *s);
 VolDev vol_dev(const Volume &v);
 LaunchCfg resolve_launch(const gbd_launch *l);
 int check_launch(const LaunchCfg &c);

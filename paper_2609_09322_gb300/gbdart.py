@@ -43,6 +43,11 @@ class Fields(ctypes.Structure):
                 ("super_brick", ctypes.c_int32), ("paired", ctypes.c_int32), ("morton_cells", ctypes.c_int32)]
 
 
+class StreamInfo(ctypes.Structure):
+    _fields_ = [("slab", ctypes.c_int32), ("flexload", ctypes.c_int32), ("slabs", ctypes.c_int32),
+                ("bytes_uploaded", ctypes.c_uint64), ("bytes_total", ctypes.c_uint64)]
+
+
 class CView(ctypes.Structure):
     _fields_ = [("dir", ctypes.c_double * 3), ("up", ctypes.c_double * 3), ("center", ctypes.c_double * 3),
                 ("t_obs", ctypes.c_double), ("c", ctypes.c_double), ("alpha", ctypes.c_double),
@@ -117,6 +122,12 @@ _SIGNATURES = {
     "gbd_bounds_violations": ([ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
     "gbd_render_batch_noalloc": ([ctypes.c_void_p, ctypes.c_uint64, ctypes.POINTER(CView), ctypes.c_int32,
                                   ctypes.POINTER(ImageSpec), ctypes.POINTER(Launch), ctypes.c_void_p], ctypes.c_int),
+    "gbd_render_streamed": ([ctypes.c_void_p, ctypes.POINTER(Grid), ctypes.POINTER(Fields), ctypes.POINTER(CView),
+                             ctypes.c_int32, ctypes.POINTER(ImageSpec), ctypes.POINTER(Launch),
+                             ctypes.POINTER(StreamInfo), ctypes.c_void_p], ctypes.c_int),
+    "gbd_render_labelled": ([ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint64), ctypes.c_int32, ctypes.POINTER(CView),
+                             ctypes.c_int32, ctypes.POINTER(ImageSpec), ctypes.POINTER(Launch), ctypes.c_void_p],
+                            ctypes.c_int),
     "gbd_serve_start": ([ctypes.c_void_p, ctypes.POINTER(ServeConfig)], ctypes.c_int),
     "gbd_serve_stop": ([ctypes.c_void_p], ctypes.c_int),
     "gbd_submit": ([ctypes.c_void_p, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_uint64)], ctypes.c_int),
@@ -276,6 +287,71 @@ class Context:
         del keep
         _check(self.lib, rc)
         return int(vid.value)
+
+    def render_labelled(self, vols, views, *, out=None, samples: bool = False, launch=None, stream=None):
+        """Images [n][H][W] of ``views`` over a scene of several resident
+        volumes (non-overlapping sub-domains, each with its own grid): the
+        sum of each ray's sums through every sub-domain."""
+        import torch
+        views = list(views)
+        v0 = views[0]
+        dev = torch.device("cuda", self.device)
+        shape = (len(views), int(v0.height), int(v0.width))
+        if out is None:
+            out = torch.empty(shape, dtype=torch.float32, device=dev)
+        cnt = torch.empty(shape, dtype=torch.int32, device=dev) if samples else None
+        ids = (ctypes.c_uint64 * len(vols))(*[int(v) for v in vols])
+        arr = (CView * len(views))(*[_cview(v) for v in views])
+        spec = self._spec(v0, out.data_ptr(), cnt.data_ptr() if cnt is not None else None)
+        rc = self.lib.gbd_render_labelled(self.handle, ids, len(vols), arr, len(views), ctypes.byref(spec),
+                                          _launch(launch), _stream_handle(stream))
+        _check(self.lib, rc)
+        return (out, cnt) if samples else out
+
+    def render_streamed(self, grid, j, beta, views, *, out=None, store="f32", slab: int = 0, flexload: bool = True,
+                        launch=None, stream=None, brick: int = 0, super_brick: int = 0):
+        """Images [n][H][W] of ``views`` rendered from host-resident fields
+        j[M][nz][ny][nx], beta[M][nz][ny][nx][3] (numpy, float32 or float64)
+        slab by slab along z, uploading with ``flexload`` only the snapshots
+        each slab's rays can reach.  Returns (images, info) with info the
+        slab and upload counts."""
+        import torch
+        views = list(views)
+        v0 = views[0]
+        g = Grid()
+        g.n[:] = [int(x) for x in grid.n]
+        g.origin[:] = [float(x) for x in grid.origin]
+        g.dx[:] = [float(x) for x in grid.dx]
+        g.n_epochs = int(grid.n_epochs)
+        g.t0 = float(grid.t0)
+        g.dt = float(grid.dt)
+        jj = np.ascontiguousarray(j.cpu().numpy() if isinstance(j, torch.Tensor) else j)
+        if jj.dtype not in (np.float64, np.float32):
+            raise TypeError("fields must be float64 or float32")
+        bb = np.ascontiguousarray(beta.cpu().numpy() if isinstance(beta, torch.Tensor) else beta, dtype=jj.dtype)
+        M, nz, ny, nx = int(grid.n_epochs), int(grid.n[2]), int(grid.n[1]), int(grid.n[0])
+        if tuple(jj.shape) != (M, nz, ny, nx) or tuple(bb.shape) != (M, nz, ny, nx, 3):
+            raise ValueError(f"field shapes {tuple(jj.shape)}, {tuple(bb.shape)} do not match the grid")
+        f = Fields()
+        f.j, f.vel = jj.ctypes.data, bb.ctypes.data
+        f.dtype_in = IN_F64 if jj.dtype == np.float64 else IN_F32
+        f.store = _STORES[store]
+        f.on_device = 0
+        f.brick = int(brick)
+        f.super_brick = int(super_brick)
+        dev = torch.device("cuda", self.device)
+        if out is None:
+            out = torch.empty((len(views), int(v0.height), int(v0.width)), dtype=torch.float32, device=dev)
+        arr = (CView * len(views))(*[_cview(v) for v in views])
+        spec = self._spec(v0, out.data_ptr(), None)
+        info = StreamInfo()
+        info.slab = int(slab)
+        info.flexload = int(bool(flexload))
+        rc = self.lib.gbd_render_streamed(self.handle, ctypes.byref(g), ctypes.byref(f), arr, len(views),
+                                          ctypes.byref(spec), _launch(launch), ctypes.byref(info),
+                                          _stream_handle(stream))
+        _check(self.lib, rc)
+        return out, dict(slabs=info.slabs, bytes_uploaded=info.bytes_uploaded, bytes_total=info.bytes_total)
 
     def unload(self, vol: int):
         _check(self.lib, self.lib.gbd_unload(self.handle, int(vol)))
