@@ -99,7 +99,10 @@ def test_uniform_emitter_over_mixed_resolutions_gives_the_chord(ctx):
         s_out = np.nanmin(np.where(sh != 0, np.maximum(t1, t2), np.inf), axis=-1)
         inside = np.all(np.where(sh == 0, (r0 >= lo) & (r0 < hi), True), axis=-1)
         chord = np.where(inside, np.maximum(s_out - s_in, 0.0), 0.0)
-        assert_parity(img, chord, what=f"labelled chord theta={theta}")
+        # A ray grazing a box corner has a chord of a few thousandths whose two
+        # ends are float32 crossings: they resolve about 1e-7 of a unit, so the
+        # absolute floor here is 2e-7 of the peak chord (bright pixels: 1e-5).
+        assert_parity(img, chord, floor_frac=0.02, what=f"labelled chord theta={theta}")
     for vol in vols:
         ctx.unload(vol)
 
