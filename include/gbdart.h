@@ -179,6 +179,8 @@ typedef struct {
     int32_t brick, super_brick, paired, morton_cells;
     uint64_t bytes;          /* device bytes held by the packed volume       */
     uint64_t record_bytes;   /* 16 (F32) or 8 (BF16_F16U)                    */
+    int32_t n_channels;      /* extra emissivity channels (gbd_load_channels) */
+    uint64_t channel_bytes;  /* device bytes of those channels               */
 } gbd_volume_desc;
 
 /* ------------------------------------------------------------ errors */
@@ -293,6 +295,23 @@ int gbd_render_streamed(gbd_ctx *ctx, const gbd_grid *grid, const gbd_fields *fi
  * one is to be cut into boxes around it. */
 int gbd_render_labelled(gbd_ctx *ctx, const gbd_volume *vols, int32_t n_vols, const gbd_view *views, int32_t n,
                         const gbd_image_spec *spec, const gbd_launch *launch, void *stream);
+
+/* Vector line-of-sight integration (Sec. 2.1: the traced field f may be a
+ * vector; the paper's code integrates a scalar).  gbd_load_channels attaches
+ * n_channels (1 or 3) more rest-frame emissivity fields to a volume, laid out
+ * [n_channels][M][nz][ny][nx] (C order) like j', sharing the volume's
+ * velocity: any finite values (a channel may be a signed component, as for
+ * polarisation-ready integrands).  They are stored as float32 in the volume's
+ * cell layout (4 bytes per cell, snapshot and channel, charged to the budget)
+ * and replace channels loaded before; a re-layout moves them along.
+ * gbd_render_vector marches each ray once and sums every channel with the same
+ * weights and Doppler factors as j' (Eq. 19 per channel): spec->out receives
+ * [n][1 + n_channels][height][width], component 0 being the image of j'.
+ * Device output only, no sample counts. */
+int gbd_load_channels(gbd_ctx *ctx, gbd_volume vol, const void *channels, int32_t n_channels, int32_t dtype_in,
+                      int32_t on_device);
+int gbd_render_vector(gbd_ctx *ctx, gbd_volume vol, const gbd_view *views, int32_t n, const gbd_image_spec *spec,
+                      const gbd_launch *launch, void *stream);
 
 /* Number of kernels the last successful render call of this thread
  * launched (graph replays count their kernels). */

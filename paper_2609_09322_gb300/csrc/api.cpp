@@ -899,6 +899,7 @@ int gbd_destroy(gbd_ctx *ctx)
         for (auto &kv : ctx->volumes) {
             if (kv.second->rec) cudaFree(kv.second->rec);
             if (kv.second->axis_off) cudaFree(kv.second->axis_off);
+            if (kv.second->chan) cudaFree(kv.second->chan);
         }
         ctx->volumes.clear();
         if (ctx->err_word) cudaFree(ctx->err_word);
@@ -1028,7 +1029,8 @@ int gbd_unload(gbd_ctx *ctx, gbd_volume vid)
     cudaDeviceSynchronize();
     cudaFree(v->rec);
     cudaFree(v->axis_off);
-    ctx->used -= v->bytes;
+    if (v->chan) cudaFree(v->chan);
+    ctx->used -= v->bytes + v->chan_bytes;
     ctx->volumes.erase(vid);
     return GBD_OK;
 }
@@ -1047,6 +1049,8 @@ int gbd_volume_info(gbd_ctx *ctx, gbd_volume vid, gbd_volume_desc *out)
     out->morton_cells = v->morton_cells;
     out->bytes = v->bytes;
     out->record_bytes = v->store == GBD_STORE_F32 ? 16 : 8;
+    out->n_channels = v->n_chan;
+    out->channel_bytes = v->chan_bytes;
     return GBD_OK;
 }
 
@@ -1066,6 +1070,127 @@ int gbd_render(gbd_ctx *ctx, gbd_volume vid, const gbd_view *view, const gbd_ima
     std::vector<ViewDev> hv(1);
     if ((rc = make_view(*vol, *view, spec->width, spec->height, spec->fov_u, spec->fov_v, hv[0]))) return rc;
     return render_direct(*ctx, *vol, hv, *spec, cfg, static_cast<cudaStream_t>(stream));
+}
+
+int gbd_load_channels(gbd_ctx *ctx, gbd_volume vid, const void *chans, int32_t n_chan, int32_t dtype_in,
+                      int32_t on_device)
+{
+    if (!ctx || !chans) return fail(GBD_ERR_INVALID, "NULL argument");
+    if (n_chan != 1 && n_chan != 3) return fail(GBD_ERR_INVALID, "n_channels must be 1 or 3");
+    if (dtype_in != GBD_IN_F64 && dtype_in != GBD_IN_F32) return fail(GBD_ERR_INVALID, "bad dtype_in");
+    std::lock_guard<std::mutex> lock(ctx->mu);
+    Volume *v = ctx->find(vid);
+    if (!v) return fail(GBD_ERR_NOTFOUND, "unknown volume %llu", static_cast<unsigned long long>(vid));
+    if (v->pinned_by_requests.load() > 0) return fail(GBD_ERR_BUSY, "volume has queued requests");
+    DeviceGuard guard(ctx->device);
+    const gbd_grid &g = v->grid;
+    std::vector<int32_t> tab;
+    long long cells = 0;
+    build_layout(g.n, v->brick, v->super_brick, tab, cells, v->morton_cells);
+    const uint64_t bytes = sizeof(float) * static_cast<uint64_t>(cells) * g.n_epochs * n_chan;
+    const uint64_t freed = v->chan_bytes;
+    if (ctx->used - freed + bytes > ctx->budget)
+        return fail(GBD_ERR_BUDGET, "channels need %llu bytes", static_cast<unsigned long long>(bytes));
+    float *dst = nullptr;
+    cudaError_t e = cudaMalloc(reinterpret_cast<void **>(&dst), bytes);
+    if (e != cudaSuccess) return cuda_fail(e, "channel allocation");
+    cudaStream_t st = ctx->load_stream;
+    const size_t esz = dtype_in == GBD_IN_F64 ? 8 : 4;
+    const size_t ncell = static_cast<size_t>(g.n[0]) * g.n[1] * g.n[2];
+    char *stage = nullptr;
+    int *bad = nullptr;
+    if (on_device) {
+        // device inputs may still be written by the caller's work on any stream
+        e = cudaDeviceSynchronize();
+    }
+    if (e == cudaSuccess) e = cudaMemsetAsync(dst, 0, bytes, st);
+    if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void **>(&bad), 256, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(bad, 0, 256, st);
+    if (e == cudaSuccess && !on_device) e = cudaMallocAsync(reinterpret_cast<void **>(&stage), ncell * esz, st);
+    for (int c = 0; c < n_chan && e == cudaSuccess; ++c)
+        for (int m = 0; m < g.n_epochs && e == cudaSuccess; ++m) {
+            const char *src = static_cast<const char *>(chans) + (static_cast<size_t>(c) * g.n_epochs + m) * ncell * esz;
+            ChanPackArgs pa;
+            std::memset(&pa, 0, sizeof(pa));
+            if (on_device) {
+                pa.src = src;
+            } else {
+                e = cudaMemcpyAsync(stage, src, ncell * esz, cudaMemcpyHostToDevice, st);
+                pa.src = stage;
+            }
+            pa.dtype_in = dtype_in;
+            for (int i = 0; i < 3; ++i) pa.n[i] = g.n[i];
+            pa.axis_off = v->axis_off;
+            pa.dst = dst + (static_cast<size_t>(c) * g.n_epochs + m) * cells;
+            pa.bad = bad;
+            if (e == cudaSuccess) e = launch_chan_pack(pa, st);
+            if (e == cudaSuccess && !on_device) e = cudaStreamSynchronize(st);  // the stage takes the next epoch
+        }
+    int h_bad = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h_bad, bad, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (stage) cudaFreeAsync(stage, st);
+    if (bad) cudaFreeAsync(bad, st);
+    cudaError_t es = cudaStreamSynchronize(st);
+    if (e == cudaSuccess) e = es;
+    if (e != cudaSuccess || h_bad) {
+        cudaFree(dst);
+        if (e != cudaSuccess) return cuda_fail(e, "channel pack");
+        return fail(GBD_ERR_INVALID, "channels: non-finite value");
+    }
+    if (v->chan) cudaFree(v->chan);
+    ctx->used = ctx->used - freed + bytes;
+    v->chan = dst;
+    v->n_chan = n_chan;
+    v->chan_stride = cells;
+    v->chan_bytes = bytes;
+    return GBD_OK;
+}
+
+int gbd_render_vector(gbd_ctx *ctx, gbd_volume vid, const gbd_view *views, int32_t n, const gbd_image_spec *spec,
+                      const gbd_launch *launch, void *stream)
+{
+    if (!ctx || !views) return fail(GBD_ERR_INVALID, "NULL argument");
+    if (n < 1 || n > (1 << 20)) return fail(GBD_ERR_INVALID, "batch size must be in [1, 2^20]");
+    int rc = check_spec(spec);
+    if (rc) return rc;
+    if (spec->out_on_host || spec->samples)
+        return fail(GBD_ERR_INVALID, "gbd_render_vector takes device output and no sample counts");
+    LaunchCfg cfg = resolve_launch(launch);
+    if ((rc = check_launch(cfg))) return rc;
+    std::lock_guard<std::mutex> lock(ctx->mu);
+    Volume *vol = ctx->find(vid);
+    if (!vol) return fail(GBD_ERR_NOTFOUND, "unknown volume %llu", static_cast<unsigned long long>(vid));
+    if (!vol->chan) return fail(GBD_ERR_INVALID, "the volume has no channels (gbd_load_channels)");
+    DeviceGuard guard(ctx->device);
+    std::vector<ViewDev> hv(static_cast<size_t>(n));
+    for (int k = 0; k < n; ++k)
+        if ((rc = make_view(*vol, views[k], spec->width, spec->height, spec->fov_u, spec->fov_v, hv[k]))) return rc;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const size_t qbytes = (static_cast<size_t>(n) * sizeof(int) + 255) / 256 * 256;
+    int *queue = nullptr;
+    cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&queue), qbytes, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(queue, 0, qbytes, st);
+    const long long plane = static_cast<long long>(spec->width) * spec->height;
+    const long long img_stride = plane * (1 + vol->n_chan);
+    const std::vector<double> work = view_works(*vol, hv, spec->width, spec->height);
+    auto a = std::make_unique<MarchArgs>();
+    int launches = 0;
+    for (int c = 0; c < march_chunks(n) && e == cudaSuccess; ++c) {
+        fill_args(*a, *vol, hv.data(), n, c, *spec, spec->out, nullptr, queue, cfg, ctx->err_word);
+        a->out = spec->out + static_cast<long long>(c) * kViewsPerLaunch * img_stride;
+        a->img_stride = img_stride;
+        a->chan = vol->chan;
+        a->chan_comp_stride = vol->chan_stride * vol->grid.n_epochs;
+        a->chan_cell_stride = vol->chan_stride;
+        e = launch_vector(*a, vol->n_chan, cfg, ctx->num_sms, work.data() + static_cast<size_t>(c) * kViewsPerLaunch,
+                          st);
+        ++launches;
+    }
+    cudaError_t ef = queue ? cudaFreeAsync(queue, st) : cudaSuccess;
+    if (e != cudaSuccess) return cuda_fail(e, "vector render");
+    if (ef != cudaSuccess) return cuda_fail(ef, "vector render scratch");
+    set_launch_count(launches);
+    return GBD_OK;
 }
 
 int gbd_render_batch(gbd_ctx *ctx, gbd_volume vid, const gbd_view *views, int32_t n, const gbd_image_spec *spec,

@@ -101,6 +101,11 @@ struct MarchArgs {
     uint32_t *samples;        // optional, same shape
     int *queue;               // persistent mode: one tile counter per view (zeroed before launch)
     int *error_word;          // checked builds: first bounds violation code
+    // vector renders (vector_kernel): extra emissivity channels of the volume
+    const float *chan;        // n_chan channels, each M blocks of chan_cell_stride floats
+    long long chan_comp_stride;   // floats per channel
+    long long chan_cell_stride;   // floats per snapshot (cells of the layout)
+    long long img_stride;     // floats between consecutive views' images (0: width * height)
     ViewDev views[kViewsPerLaunch];
 };
 static_assert(sizeof(MarchArgs) <= 32764, "march launch arguments exceed the kernel parameter limit");
@@ -193,6 +198,10 @@ struct KernelLaunch {
 cudaError_t plan_march(MarchArgs &a, const LaunchCfg &cfg, int num_sms, const double *work, KernelLaunch &k);
 cudaError_t launch_march(MarchArgs &a, const LaunchCfg &cfg, int num_sms, const double *work, cudaStream_t stream);
 cudaError_t launch_wave(const WaveArgs &a, const LaunchCfg &cfg, cudaStream_t stream);
+// Vector render: n_chan (1 or 3) extra channels besides j'; image v's
+// component c at out + v * img_stride + c * width * height.
+cudaError_t launch_vector(MarchArgs &a, int n_chan, const LaunchCfg &cfg, int num_sms, const double *work,
+                          cudaStream_t stream);
 // Region schedule: the caller has filled everything but the grid, which
 // launch_region derives from cta_begin and the region counts.
 cudaError_t launch_region(const RegionArgs &a, const LaunchCfg &cfg, cudaStream_t stream);
@@ -213,6 +222,16 @@ struct PackArgs {
 };
 cudaError_t launch_pack(const PackArgs &a, cudaStream_t stream);
 
+struct ChanPackArgs {
+    const void *src;          // one channel, one epoch, [nz][ny][nx]
+    int dtype_in;             // GBD_IN_F64 / GBD_IN_F32
+    int n[3];
+    const int32_t *axis_off;  // device tables
+    float *dst;               // that channel's epoch block
+    int *bad;                 // device flag: set to 1 on a non-finite value
+};
+cudaError_t launch_chan_pack(const ChanPackArgs &a, cudaStream_t stream);
+
 struct RelayoutArgs {
     const void *src;          // whole record array in the old layout
     void *dst;                // whole record array in the new layout
@@ -222,7 +241,7 @@ struct RelayoutArgs {
     int src_paired, dst_paired;
     int m;                    // epoch being copied
     int n[3];
-    int record_bytes;         // 16 or 8
+    int record_bytes;         // 16 or 8 (records), 4 (channel values, unpaired)
 };
 cudaError_t launch_relayout(const RelayoutArgs &a, cudaStream_t stream);
 

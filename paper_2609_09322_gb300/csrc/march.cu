@@ -86,14 +86,20 @@ struct Record<GBD_STORE_F32> {
     // D^(2 - alpha) j' with D = sqrt(1 - beta^2) / (1 + beta . s_hat) (Eq. 14).
     // 1 + beta.s_hat and 1 - beta^2 are formed with fused multiply-adds so
     // each is rounded once near its (possibly small) value.
-    static __device__ __forceinline__ float boosted(const T r, const BoostConsts &c)
+    static __device__ __forceinline__ float emissivity(const T r) { return r.x; }
+    // D^(2 - alpha), or 1 without beaming
+    static __device__ __forceinline__ float boost(const T r, const BoostConsts &c)
     {
-        if (!c.beaming) return r.x;
+        if (!c.beaming) return 1.0f;
         float den = fmaf(r.y, c.shx, fmaf(r.z, c.shy, fmaf(r.w, c.shz, 1.0f)));
         den += fmaf(r.y, c.slx, fmaf(r.z, c.sly, r.w * c.slz));
         const float inv_g2 = fmaf(-r.y, r.y, fmaf(-r.z, r.z, fmaf(-r.w, r.w, 1.0f)));
         const float log2_d = fmaf(0.5f, lg2_approx(inv_g2), -lg2_approx(den));
-        return r.x * ex2_approx(c.expo * log2_d);
+        return ex2_approx(c.expo * log2_d);
+    }
+    static __device__ __forceinline__ float boosted(const T r, const BoostConsts &c)
+    {
+        return emissivity(r) * boost(r, c);
     }
 };
 
@@ -118,10 +124,11 @@ struct Record<GBD_STORE_BF16_F16U> {
     // (Gamma + |u.s_hat|) / (1 + |u|^2 - (u.s_hat)^2), which has no cancellation.
     // s_hat enters rounded to float: its rounding (6e-8) is far below the
     // float16 resolution of u (5e-4 relative), unlike in the float32 record.
-    static __device__ __forceinline__ float boosted(const T r, const BoostConsts &c)
+    static __device__ __forceinline__ float emissivity(const T r) { return __uint_as_float(r.x << 16); }
+    // D^(2 - alpha), or 1 without beaming
+    static __device__ __forceinline__ float boost(const T r, const BoostConsts &c)
     {
-        const float j = __uint_as_float(r.x << 16);
-        if (!c.beaming) return j;
+        if (!c.beaming) return 1.0f;
         const float ux = __half2float(__ushort_as_half(static_cast<unsigned short>(r.x >> 16)));
         const float uy = __half2float(__ushort_as_half(static_cast<unsigned short>(r.y & 0xffffu)));
         const float uz = __half2float(__ushort_as_half(static_cast<unsigned short>(r.y >> 16)));
@@ -130,7 +137,11 @@ struct Record<GBD_STORE_BF16_F16U> {
         const float gp = sqrt_approx(1.0f + uu) + fabsf(us);
         const float perp = 1.0f + fmaf(-us, us, uu);
         const float log2_d = (us < 0.f) ? (lg2_approx(gp) - lg2_approx(perp)) : -lg2_approx(gp);
-        return j * ex2_approx(c.expo * log2_d);
+        return ex2_approx(c.expo * log2_d);
+    }
+    static __device__ __forceinline__ float boosted(const T r, const BoostConsts &c)
+    {
+        return emissivity(r) * boost(r, c);
     }
 };
 
@@ -237,10 +248,21 @@ __device__ __forceinline__ RayBox grid_box(const VolDev &vol, const ViewDev &V)
 // the box, without the prefactor, to out_img[pixel] if the ray sampled at
 // least one cell there (one region per slot and ray, so the add lands on
 // zero).  tab points at the march tables (shared memory when SMEM).
-template <int STORE, int DEPTH, bool PAIRED, bool SMEM, bool PARTIAL = false>
+//
+// NCH > 0 (vector renders, Sec. 2.1): the volume carries NCH more emissivity
+// channels sharing its velocity; each is summed with the same weights and
+// Doppler factors as j' (Eq. 19 per channel) into component c + 1 of the
+// pixel, at out_img + (c + 1) * width * height.
+struct ChanPtrs {
+    const float *chan;
+    long long comp_stride, cell_stride;
+};
+
+template <int STORE, int DEPTH, bool PAIRED, bool SMEM, bool PARTIAL = false, int NCH = 0>
 __device__ __forceinline__ void march_ray(const VolDev &vol, const ViewDev &V, const RayBox &B, int p, int q,
                                           int width, int height, float *out_img, uint32_t *cnt_img, int *err_word,
-                                          const int32_t *__restrict__ tab, bool accumulate = false)
+                                          const int32_t *__restrict__ tab, bool accumulate = false,
+                                          const ChanPtrs ch = ChanPtrs{nullptr, 0, 0})
 {
     using Rec = Record<STORE>;
     const bool in_image = (p < width) && (q < height);
@@ -375,6 +397,9 @@ __device__ __forceinline__ void march_ray(const VolDev &vol, const ViewDev &V, c
 
     float acc = 0.f, comp = 0.f;
     uint32_t count = 0;
+    float cacc[NCH > 0 ? NCH : 1], ccomp[NCH > 0 ? NCH : 1];
+#pragma unroll
+    for (int c = 0; c < (NCH > 0 ? NCH : 1); ++c) cacc[c] = ccomp[c] = 0.f;
 
     // ---------------- the march, float32 per cell ----------------
     // Per cell: the nearest face, the chord from the previous exit, the epoch
@@ -382,6 +407,7 @@ __device__ __forceinline__ void march_ray(const VolDev &vol, const ViewDev &V, c
     // ray ends past the last time that reaches a snapshot or at a sentinel.
     while (__any_sync(kFull, alive)) {
         long long off[DEPTH];
+        long long coff[DEPTH];  // channel offset (vector renders)
         float wgt[DEPTH], dsv[DEPTH];
         bool has_lo[DEPTH], has_hi[DEPTH];
 #pragma unroll
@@ -389,6 +415,7 @@ __device__ __forceinline__ void march_ray(const VolDev &vol, const ViewDev &V, c
             has_lo[d] = false;
             has_hi[d] = false;
             off[d] = 0;
+            coff[d] = 0;
             wgt[d] = 0.f;
             dsv[d] = 0.f;
             if (alive) {
@@ -419,6 +446,7 @@ __device__ __forceinline__ void march_ray(const VolDev &vol, const ViewDev &V, c
                     // mb + 1 side by side in block mb + 1
                     off[d] = PAIRED ? static_cast<long long>(mb + 1) * es + 2LL * sum
                                     : static_cast<long long>(mb) * es + sum;
+                    if constexpr (NCH > 0) coff[d] = static_cast<long long>(mb) * ch.cell_stride + sum;
                     wgt[d] = w;
                     dsv[d] = ds;
                 }
@@ -457,16 +485,49 @@ __device__ __forceinline__ void march_ray(const VolDev &vol, const ViewDev &V, c
                 rhi[d] = has_hi[d] ? Rec::load(recs, off[d] + es) : Rec::zero();
             }
         }
+        float clo[DEPTH][NCH > 0 ? NCH : 1], chi[DEPTH][NCH > 0 ? NCH : 1];
+        if constexpr (NCH > 0) {
+#pragma unroll
+            for (int d = 0; d < DEPTH; ++d)
+#pragma unroll
+                for (int c = 0; c < NCH; ++c) {
+                    const float *base = ch.chan + c * ch.comp_stride + coff[d];
+                    clo[d][c] = has_lo[d] ? __ldg(base) : 0.f;
+                    chi[d][c] = has_hi[d] ? __ldg(base + ch.cell_stride) : 0.f;
+                }
+        }
 #pragma unroll
         for (int d = 0; d < DEPTH; ++d) {
             if (has_lo[d] || has_hi[d]) {
-                const float vlo = has_lo[d] ? Rec::boosted(rlo[d], bc) : 0.f;
-                const float vhi = has_hi[d] ? Rec::boosted(rhi[d], bc) : 0.f;
-                const float v = fmaf(wgt[d], vhi - vlo, vlo);       // Eq. 8
-                const float y = fmaf(v, dsv[d], -comp);             // compensated sum
-                const float t = acc + y;
-                comp = (t - acc) - y;
-                acc = t;
+                if constexpr (NCH == 0) {
+                    const float vlo = has_lo[d] ? Rec::boosted(rlo[d], bc) : 0.f;
+                    const float vhi = has_hi[d] ? Rec::boosted(rhi[d], bc) : 0.f;
+                    const float v = fmaf(wgt[d], vhi - vlo, vlo);       // Eq. 8
+                    const float y = fmaf(v, dsv[d], -comp);             // compensated sum
+                    const float t = acc + y;
+                    comp = (t - acc) - y;
+                    acc = t;
+                } else {
+                    // the Doppler factor of each snapshot serves every channel
+                    const float blo = has_lo[d] ? Rec::boost(rlo[d], bc) : 0.f;
+                    const float bhi = has_hi[d] ? Rec::boost(rhi[d], bc) : 0.f;
+                    const float vlo = has_lo[d] ? Rec::emissivity(rlo[d]) * blo : 0.f;
+                    const float vhi = has_hi[d] ? Rec::emissivity(rhi[d]) * bhi : 0.f;
+                    const float v = fmaf(wgt[d], vhi - vlo, vlo);
+                    const float y = fmaf(v, dsv[d], -comp);
+                    const float t = acc + y;
+                    comp = (t - acc) - y;
+                    acc = t;
+#pragma unroll
+                    for (int c = 0; c < NCH; ++c) {
+                        const float ulo = clo[d][c] * blo, uhi = chi[d][c] * bhi;
+                        const float u = fmaf(wgt[d], uhi - ulo, ulo);
+                        const float yc = fmaf(u, dsv[d], -ccomp[c]);
+                        const float tc = cacc[c] + yc;
+                        ccomp[c] = (tc - cacc[c]) - yc;
+                        cacc[c] = tc;
+                    }
+                }
                 ++count;
             }
         }
@@ -482,6 +543,11 @@ __device__ __forceinline__ void march_ray(const VolDev &vol, const ViewDev &V, c
         } else {
             out_img[pix] = V.prefactor * acc;
             if (cnt_img) cnt_img[pix] = count;
+        }
+        if constexpr (NCH > 0) {
+            const long long plane = static_cast<long long>(width) * height;
+#pragma unroll
+            for (int c = 0; c < NCH; ++c) out_img[(c + 1) * plane + pix] = V.prefactor * cacc[c];
         }
     }
 }
@@ -517,7 +583,7 @@ __global__ void __launch_bounds__(256, MINB) march_kernel(const __grid_constant_
     const ViewDev &V = a.views[vi];
     const RayBox box = grid_box(a.vol, V);
     const int tiles = a.tiles_x * a.tiles_y;
-    const long long img = static_cast<long long>(vi) * a.width * a.height;
+    const long long img = static_cast<long long>(vi) * (a.img_stride ? a.img_stride : static_cast<long long>(a.width) * a.height);
     float *out = a.out + img;
     uint32_t *cnt = a.samples ? a.samples + img : nullptr;
     int tile = cb * wpc + warp;
@@ -534,6 +600,49 @@ __global__ void __launch_bounds__(256, MINB) march_kernel(const __grid_constant_
         const int q = ty * a.packet_h + lane / a.packet_w;
         march_ray<STORE, DEPTH, PAIRED, true>(a.vol, V, box, p, q, a.width, a.height, out, cnt, a.error_word, s_tab,
                                               a.accumulate != 0);
+        if (!a.persistent) break;
+    }
+}
+
+// Vector renders: march_kernel's work split with NCH extra channels summed
+// along every ray (depth 2, persistent, compiler's register budget).
+template <int STORE, int NCH, bool PAIRED>
+__global__ void __launch_bounds__(256, 1) vector_kernel(const __grid_constant__ MarchArgs a)
+{
+    extern __shared__ int32_t s_tab[];
+    const int ntab = march_table_entries(a.vol.n);
+    for (int i = threadIdx.x; i < ntab; i += blockDim.x) s_tab[i] = a.vol.mtab[i];
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int wpc = blockDim.x >> 5;
+    const int b = static_cast<int>(blockIdx.x);
+    int vi = 0, hi = a.n_views - 1;
+    while (vi < hi) {
+        const int mid = (vi + hi + 1) >> 1;
+        if (a.cta_begin[mid] <= b) vi = mid;
+        else hi = mid - 1;
+    }
+    const int cb = b - a.cta_begin[vi];
+    const ViewDev &V = a.views[vi];
+    const RayBox box = grid_box(a.vol, V);
+    const int tiles = a.tiles_x * a.tiles_y;
+    float *out = a.out + static_cast<long long>(vi) * a.img_stride;
+    const ChanPtrs ch{a.chan, a.chan_comp_stride, a.chan_cell_stride};
+    int tile = cb * wpc + warp;
+    for (;;) {
+        if (a.persistent) {
+            int it = 0;
+            if (lane == 0) it = atomicAdd(a.queue + vi, 1);
+            tile = __shfl_sync(kFull, it, 0);
+        }
+        if (tile >= tiles) break;
+        const int tx = tile % a.tiles_x;
+        const int ty = tile / a.tiles_x;
+        const int p = tx * a.packet_w + lane % a.packet_w;
+        const int q = ty * a.packet_h + lane / a.packet_w;
+        march_ray<STORE, 2, PAIRED, true, false, NCH>(a.vol, V, box, p, q, a.width, a.height, out, nullptr,
+                                                       a.error_word, s_tab, false, ch);
         if (!a.persistent) break;
     }
 }
@@ -732,6 +841,18 @@ void *select_region(int store, int depth, int capped, int paired)
     return nullptr;
 }
 
+template <int NCH>
+void *select_vector_store(int store, int paired)
+{
+    if (store == GBD_STORE_F32)
+        return paired ? reinterpret_cast<void *>(&vector_kernel<GBD_STORE_F32, NCH, true>)
+                      : reinterpret_cast<void *>(&vector_kernel<GBD_STORE_F32, NCH, false>);
+    if (store == GBD_STORE_BF16_F16U)
+        return paired ? reinterpret_cast<void *>(&vector_kernel<GBD_STORE_BF16_F16U, NCH, true>)
+                      : reinterpret_cast<void *>(&vector_kernel<GBD_STORE_BF16_F16U, NCH, false>);
+    return nullptr;
+}
+
 void *select_wave(int depth, int capped)
 {
     if (depth == 1) return capped ? reinterpret_cast<void *>(&wave_kernel<1, 3>) : reinterpret_cast<void *>(&wave_kernel<1, 1>);
@@ -749,6 +870,27 @@ cudaError_t launch_wave(const WaveArgs &a, const LaunchCfg &cfg, cudaStream_t st
     void *params[] = {const_cast<WaveArgs *>(&a)};
     return cudaLaunchKernel(k, dim3(static_cast<unsigned>(a.total_ctas)), dim3(32 * cfg.cta_warps), params, 0,
                             stream);
+}
+
+cudaError_t launch_vector(MarchArgs &a, int n_chan, const LaunchCfg &cfg, int num_sms, const double *work,
+                          cudaStream_t stream)
+{
+    void *k = n_chan == 1 ? select_vector_store<1>(a.vol.store, a.vol.paired)
+                          : (n_chan == 3 ? select_vector_store<3>(a.vol.store, a.vol.paired) : nullptr);
+    if (!k) return cudaErrorInvalidValue;
+    // grid as planned for the scalar kernel of the same configuration
+    LaunchCfg c = cfg;
+    c.depth = 2;
+    c.regcap = 0;
+    KernelLaunch L;
+    cudaError_t e = plan_march(a, c, num_sms, work, L);
+    if (e != cudaSuccess) return e;
+    if (L.smem > 48 * 1024) {
+        e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, L.smem);
+        if (e != cudaSuccess) return e;
+    }
+    void *params[] = {&a};
+    return cudaLaunchKernel(k, L.grid, L.block, params, L.smem, stream);
 }
 
 cudaError_t launch_region(const RegionArgs &a, const LaunchCfg &cfg, cudaStream_t stream)

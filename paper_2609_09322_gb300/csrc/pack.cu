@@ -81,6 +81,29 @@ __global__ void pack_kernel(const PackArgs a)
     }
 }
 
+// One epoch of one extra emissivity channel (vector renders): a float per
+// cell at the cell's layout offset; any finite value (a channel may be a
+// signed component).
+template <typename TIN>
+__global__ void chan_pack_kernel(const ChanPackArgs a)
+{
+    const int nx = a.n[0], ny = a.n[1], nz = a.n[2];
+    const long long ncell = static_cast<long long>(nx) * ny * nz;
+    const TIN *in = static_cast<const TIN *>(a.src);
+    for (long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; i < ncell;
+         i += static_cast<long long>(gridDim.x) * blockDim.x) {
+        const int ix = static_cast<int>(i % nx);
+        const long long r = i / nx;
+        const int iy = static_cast<int>(r % ny);
+        const int iz = static_cast<int>(r / ny);
+        const long long cell = static_cast<long long>(a.axis_off[ix]) + a.axis_off[nx + iy] + a.axis_off[nx + ny + iz];
+        const float v = __double2float_rn(static_cast<double>(in[i]));
+        const bool ok = isfinite(v);
+        a.dst[cell] = ok ? v : 0.f;
+        if (!ok) atomicExch(a.bad, 1);
+    }
+}
+
 // Copies every record of one epoch from one layout to another (the tables of
 // both layouts have the same n_x + n_y + n_z entries).
 template <typename R>
@@ -121,7 +144,8 @@ cudaError_t launch_relayout(const RelayoutArgs &a, cudaStream_t stream)
     RelayoutArgs args = a;
     void *params[] = {&args};
     void *k = a.record_bytes == 16 ? reinterpret_cast<void *>(&relayout_kernel<uint4>)
-                                   : reinterpret_cast<void *>(&relayout_kernel<uint2>);
+                                   : (a.record_bytes == 8 ? reinterpret_cast<void *>(&relayout_kernel<uint2>)
+                                                          : reinterpret_cast<void *>(&relayout_kernel<float>));
     return cudaLaunchKernel(k, dim3(static_cast<unsigned>(blocks)), dim3(256), params, 0, stream);
 }
 
@@ -135,6 +159,19 @@ cudaError_t launch_pack(const PackArgs &a, cudaStream_t stream)
     void *params[] = {&args};
     void *k = a.dtype_in == GBD_IN_F64 ? reinterpret_cast<void *>(&pack_kernel<double>)
                                        : reinterpret_cast<void *>(&pack_kernel<float>);
+    return cudaLaunchKernel(k, dim3(static_cast<unsigned>(blocks)), dim3(256), params, 0, stream);
+}
+
+cudaError_t launch_chan_pack(const ChanPackArgs &a, cudaStream_t stream)
+{
+    const long long ncell = static_cast<long long>(a.n[0]) * a.n[1] * a.n[2];
+    long long blocks = (ncell + 255) / 256;
+    if (blocks > 65535LL * 16) blocks = 65535LL * 16;
+    if (blocks < 1) return cudaSuccess;
+    ChanPackArgs args = a;
+    void *params[] = {&args};
+    void *k = a.dtype_in == GBD_IN_F64 ? reinterpret_cast<void *>(&chan_pack_kernel<double>)
+                                       : reinterpret_cast<void *>(&chan_pack_kernel<float>);
     return cudaLaunchKernel(k, dim3(static_cast<unsigned>(blocks)), dim3(256), params, 0, stream);
 }
 

@@ -26,6 +26,10 @@ struct Volume {
     int32_t *axis_off = nullptr;     // per-axis offset tables (n_x + n_y + n_z), then the march tables
     long long epoch_stride = 0;      // records per block (epoch, or epoch pair)
     uint64_t bytes = 0;              // device bytes charged to the budget
+    float *chan = nullptr;           // extra emissivity channels (vector renders), unpaired layout
+    int n_chan = 0;
+    long long chan_stride = 0;       // floats per snapshot of one channel
+    uint64_t chan_bytes = 0;         // device bytes of the channels (charged to the budget)
     std::atomic<int> pinned_by_requests{0};  // queued or running serving requests using it
 };
 

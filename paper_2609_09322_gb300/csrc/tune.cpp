@@ -139,8 +139,33 @@ int relayout_volume(Ctx &ctx, Volume &vol, gbd_volume vid, int B, int S, int pai
         return cuda_fail(e, "re-layout table allocation");
     }
     cudaStream_t st = ctx.load_stream;
+    // extra emissivity channels move with the records
+    float *chan = nullptr;
+    const long long cells_new = paired ? stride / 2 : stride;
+    if (vol.chan) {
+        e = cudaMalloc(reinterpret_cast<void **>(&chan), vol.chan_bytes / static_cast<uint64_t>(vol.chan_stride) *
+                                                            static_cast<uint64_t>(cells_new));
+        if (e != cudaSuccess) {
+            cudaFree(rec);
+            cudaFree(off);
+            return cuda_fail(e, "re-layout channel allocation");
+        }
+    }
     e = cudaMemcpyAsync(off, tab.data(), tab_bytes, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(rec, 0, bytes, st);
+    if (e == cudaSuccess && chan)
+        e = cudaMemsetAsync(chan, 0, vol.chan_bytes / static_cast<uint64_t>(vol.chan_stride) * cells_new, st);
+    for (int k = 0; k < vol.n_chan * vol.grid.n_epochs && e == cudaSuccess; ++k) {
+        RelayoutArgs ra;
+        std::memset(&ra, 0, sizeof(ra));
+        ra.src = vol.chan + static_cast<size_t>(k) * vol.chan_stride;
+        ra.dst = chan + static_cast<size_t>(k) * cells_new;
+        ra.src_off = vol.axis_off;
+        ra.dst_off = off;
+        for (int i = 0; i < 3; ++i) ra.n[i] = vol.grid.n[i];
+        ra.record_bytes = 4;
+        e = launch_relayout(ra, st);
+    }
     for (int m = 0; m < vol.grid.n_epochs && e == cudaSuccess; ++m) {
         RelayoutArgs ra;
         std::memset(&ra, 0, sizeof(ra));
@@ -162,6 +187,7 @@ int relayout_volume(Ctx &ctx, Volume &vol, gbd_volume vid, int B, int S, int pai
     if (e != cudaSuccess) {
         cudaFree(rec);
         cudaFree(off);
+        if (chan) cudaFree(chan);
         return cuda_fail(e, "re-layout");
     }
     drop_graphs_for(ctx, vid);
@@ -171,6 +197,14 @@ int relayout_volume(Ctx &ctx, Volume &vol, gbd_volume vid, int B, int S, int pai
     ctx.used -= vol.bytes;
     vol.rec = rec;
     vol.axis_off = off;
+    if (chan) {
+        cudaFree(vol.chan);
+        ctx.used -= vol.chan_bytes;
+        vol.chan_bytes = vol.chan_bytes / static_cast<uint64_t>(vol.chan_stride) * cells_new;
+        ctx.used += vol.chan_bytes;
+        vol.chan = chan;
+        vol.chan_stride = cells_new;
+    }
     vol.epoch_stride = stride;
     vol.brick = B;
     vol.super_brick = S;

@@ -101,7 +101,7 @@ class VolumeDesc(ctypes.Structure):
     _fields_ = [("grid", Grid), ("store", ctypes.c_int32), ("brick", ctypes.c_int32),
                 ("super_brick", ctypes.c_int32), ("paired", ctypes.c_int32), ("morton_cells", ctypes.c_int32),
                 ("bytes", ctypes.c_uint64),
-                ("record_bytes", ctypes.c_uint64)]
+                ("record_bytes", ctypes.c_uint64), ("n_channels", ctypes.c_int32), ("channel_bytes", ctypes.c_uint64)]
 
 
 _lock = threading.Lock()
@@ -128,6 +128,10 @@ _SIGNATURES = {
     "gbd_render_labelled": ([ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint64), ctypes.c_int32, ctypes.POINTER(CView),
                              ctypes.c_int32, ctypes.POINTER(ImageSpec), ctypes.POINTER(Launch), ctypes.c_void_p],
                             ctypes.c_int),
+    "gbd_load_channels": ([ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
+                           ctypes.c_int32], ctypes.c_int),
+    "gbd_render_vector": ([ctypes.c_void_p, ctypes.c_uint64, ctypes.POINTER(CView), ctypes.c_int32,
+                           ctypes.POINTER(ImageSpec), ctypes.POINTER(Launch), ctypes.c_void_p], ctypes.c_int),
     "gbd_serve_start": ([ctypes.c_void_p, ctypes.POINTER(ServeConfig)], ctypes.c_int),
     "gbd_serve_stop": ([ctypes.c_void_p], ctypes.c_int),
     "gbd_submit": ([ctypes.c_void_p, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_uint64)], ctypes.c_int),
@@ -288,6 +292,43 @@ class Context:
         _check(self.lib, rc)
         return int(vid.value)
 
+    def load_channels(self, vol: int, channels):
+        """Attach extra emissivity channels [K][M][nz][ny][nx] (K = 1 or 3;
+        numpy or torch, float32 or float64) to a volume for vector renders."""
+        import torch
+        if isinstance(channels, torch.Tensor) and channels.is_cuda:
+            cc = channels.contiguous()
+            if cc.dtype not in (torch.float64, torch.float32):
+                raise TypeError("channels must be float64 or float32")
+            dtype_in, ptr, on_device = (IN_F64 if cc.dtype == torch.float64 else IN_F32), cc.data_ptr(), 1
+        else:
+            cc = np.ascontiguousarray(channels.cpu().numpy() if isinstance(channels, torch.Tensor) else channels)
+            if cc.dtype not in (np.float64, np.float32):
+                raise TypeError("channels must be float64 or float32")
+            dtype_in, ptr, on_device = (IN_F64 if cc.dtype == np.float64 else IN_F32), cc.ctypes.data, 0
+        info = self.volume_info(vol)
+        want = (int(info["n_epochs"]), int(info["n"][2]), int(info["n"][1]), int(info["n"][0]))
+        if cc.ndim != 5 or tuple(cc.shape[1:]) != want:
+            raise ValueError(f"channels must be [K]{list(want)}, got {tuple(cc.shape)}")
+        _check(self.lib, self.lib.gbd_load_channels(self.handle, int(vol), ptr, int(cc.shape[0]), dtype_in, on_device))
+
+    def render_vector(self, vol: int, views, *, out=None, launch=None, stream=None):
+        """Images [n][1 + K][H][W]: component 0 of j', components 1.. of the
+        volume's extra channels, all marched along each ray at once."""
+        import torch
+        views = list(views)
+        v0 = views[0]
+        k = int(self.volume_info(vol).get("channels", 0))
+        if out is None:
+            out = torch.empty((len(views), 1 + k, int(v0.height), int(v0.width)), dtype=torch.float32,
+                              device=torch.device("cuda", self.device))
+        arr = (CView * len(views))(*[_cview(v) for v in views])
+        spec = self._spec(v0, out.data_ptr(), None)
+        rc = self.lib.gbd_render_vector(self.handle, int(vol), arr, len(views), ctypes.byref(spec), _launch(launch),
+                                        _stream_handle(stream))
+        _check(self.lib, rc)
+        return out
+
     def render_labelled(self, vols, views, *, out=None, samples: bool = False, launch=None, stream=None):
         """Images [n][H][W] of ``views`` over a scene of several resident
         volumes (non-overlapping sub-domains, each with its own grid): the
@@ -361,7 +402,7 @@ class Context:
         _check(self.lib, self.lib.gbd_volume_info(self.handle, int(vol), ctypes.byref(d)))
         return dict(n=tuple(d.grid.n), n_epochs=d.grid.n_epochs, store=d.store, brick=d.brick,
                     super_brick=d.super_brick, paired=d.paired, morton_cells=d.morton_cells, bytes=int(d.bytes),
-                    record_bytes=int(d.record_bytes))
+                    record_bytes=int(d.record_bytes), channels=int(d.n_channels), channel_bytes=int(d.channel_bytes))
 
     # -- rendering
     def _spec(self, view, out_ptr, samples_ptr, on_host=False) -> ImageSpec:
