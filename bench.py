@@ -14,6 +14,13 @@ Workloads (synthetic, seeded; see gen/):
   batched               384^3 x 32 turbulent jet, float32, 256 views of 256^2
                         on a Fibonacci sphere in one persistent launch.
 
+Forms (--form) of the same workload's march:
+  batch (default)  the batch render of every view, volume resident.
+  streamed         the volume stays in pinned host memory and is uploaded slab
+                   by slab with flexload, marched slab by slab (out-of-core).
+  labelled         the volume given as two sub-domains (its halves along x).
+  vector           three extra emissivity channels marched with j'.
+
 Prints one JSON line.  --impl reference times the FP64 CPU oracle on a
 bounded sample of the same workload instead.
 """
@@ -229,7 +236,46 @@ def run_gpu(args, rank: int, world: int):
     del cnt
     out = torch.empty((n_views, views[0].height, views[0].width), dtype=torch.float32, device=f"cuda:{dev}")
 
-    if args.per_image:
+    form_note = {}
+    extra_bytes_per_sample = 0
+    if args.form == "streamed":
+        # the series in pinned host memory; each step uploads and marches it slab by slab
+        j_h = torch.from_numpy(np.ascontiguousarray(wl["j"], dtype=np.float32)).pin_memory()
+        b_h = torch.from_numpy(np.ascontiguousarray(wl["beta"], dtype=np.float32)).pin_memory()
+        ctx.unload(vol)
+        s_launch = launch or {"packet": (4, 8), "cta_warps": 4, "depth": 2, "persistent": 1, "regcap": 1}
+        s_info = {}
+
+        def step():
+            _, s = ctx.render_streamed(wl["grid"], j_h.numpy(), b_h.numpy(), views, out=out, store=wl["store"],
+                                       slab=args.slab, flexload=True, launch=s_launch, stream=stream)
+            s_info.update(s)
+        step()
+        form_note = {"form": "streamed", "slab": args.slab, "flexload": True}
+    elif args.form == "labelled":
+        g = wl["grid"]
+        cut = g.n[0] // 2
+        halves = []
+        for lo, hi in ((0, cut), (cut, g.n[0])):
+            sub = type(g)(n=(hi - lo, g.n[1], g.n[2]), origin=(g.origin[0] + lo * g.dx[0], g.origin[1], g.origin[2]),
+                          dx=g.dx, n_epochs=g.n_epochs, t0=g.t0, dt=g.dt)
+            halves.append(ctx.load_snapshots(sub, np.ascontiguousarray(wl["j"][..., lo:hi]),
+                                             np.ascontiguousarray(wl["beta"][..., lo:hi, :]), store=wl["store"],
+                                             brick=brick, super_brick=sbrick, paired=bool(paired)))
+
+        def step():
+            ctx.render_labelled(halves, views, out=out, launch=launch, stream=stream)
+        form_note = {"form": "labelled", "sub_domains": 2}
+    elif args.form == "vector":
+        jj = np.ascontiguousarray(wl["j"], dtype=np.float32)
+        ctx.load_channels(vol, np.stack([2.0 * jj, jj * jj, -jj]))
+        vout = torch.empty((n_views, 4, views[0].height, views[0].width), dtype=torch.float32, device=f"cuda:{dev}")
+        extra_bytes_per_sample = 3 * 4 * (2 if wl["lookback"] else 1)
+
+        def step():
+            ctx.render_vector(vol, views, out=vout, launch=launch, stream=stream)
+        form_note = {"form": "vector", "channels": 1 + 3}
+    elif args.per_image:
         # the plain per-image march: one render call per view, no batching
         def step():
             for k, v in enumerate(views):
@@ -270,33 +316,52 @@ def run_gpu(args, rank: int, world: int):
     launches = args.steps * (n_views if args.per_image else ctx.last_launch_count())
 
     # end to end through the public API with host buffers
-    host = torch.empty((n_views, views[0].height, views[0].width), dtype=torch.float32, pin_memory=True)
+    if args.form == "batch":
+        host = torch.empty((n_views, views[0].height, views[0].width), dtype=torch.float32, pin_memory=True)
+
+        def e2e_step():
+            ctx.render_batch_host(vol, views, host, launch=launch, stream=stream)
+    else:
+        # the form's own call, then the images read back into pinned memory
+        dev_img = vout if args.form == "vector" else out
+        host = torch.empty(dev_img.shape, dtype=torch.float32, pin_memory=True)
+
+        def e2e_step():
+            step()
+            with torch.cuda.stream(stream):
+                host.copy_(dev_img, non_blocking=True)
     for _ in range(2):
-        ctx.render_batch_host(vol, views, host, launch=launch, stream=stream)
+        e2e_step()
     stream.synchronize()
     e2e_steps = max(3, min(args.steps, 20))
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
-        ctx.render_batch_host(vol, views, host, launch=launch, stream=stream)
+        e2e_step()
         stream.synchronize()
     e2e_s = (time.perf_counter() - t0) / e2e_steps
     view_bytes = 216 * n_views  # the per-view constants travel to the device in the launch parameters
+    if args.form == "streamed":
+        view_bytes += int(s_info.get("bytes_uploaded", 0))  # the series itself, slab by slab
     img_bytes = host.numel() * 4
 
     rec = RECORD_BYTES[wl["store"]]
-    bytes_per_sample = rec * (2 if wl["lookback"] else 1)
+    bytes_per_sample = rec * (2 if wl["lookback"] else 1) + extra_bytes_per_sample
     alg_bytes = samples_per_step * bytes_per_sample
     kernel_ms = statistics.median(per_step)
     achieved = alg_bytes / (kernel_ms * 1e-3) / 1e9
     peak, peak_kind = measured_peak_hbm()
-    traffic = recorded_traffic(args.workload)
+    traffic = recorded_traffic(args.workload) if args.form == "batch" and not args.per_image else None
     value = world * samples_per_step / (ms_per_step * 1e-3) / 1e9
     result = {
         "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32" if wl["store"] == "f32" else "bf16/f16 storage, f32 math",
         "data": "synthetic (seeded generators in gen/)",
-        "config": {"workload": wl["desc"] + ("; plain per-image renders" if args.per_image else ""),
+        "config": {"workload": wl["desc"] + ("; plain per-image renders" if args.per_image else "")
+                   + {"batch": "", "streamed": f"; out-of-core: series in pinned host memory, {args.slab}-cell "
+                                                f"slabs uploaded with flexload each step",
+                      "labelled": "; labelled: two sub-domains (halves along x)",
+                      "vector": "; vector: j' and three extra emissivity channels per ray"}[args.form],
                    "images_per_step": n_views,
                    "cell_samples_per_step": samples_per_step,
                    "volume_bytes": info["bytes"], "l2": "inputs larger than L2 (resident volume %.1f GB)"
@@ -316,6 +381,11 @@ def run_gpu(args, rank: int, world: int):
                 "note": "render_batch with host output: per-view constants H2D in the launch parameters, "
                         "images D2H into pinned memory, volume resident"},
         "gpu_launches": launches,
+        **({"form": form_note} if form_note else {}),
+        **({"streamed": {"bytes_uploaded_per_step": int(s_info.get("bytes_uploaded", 0)),
+                         "bytes_of_series": int(s_info.get("bytes_total", 0)), "slabs": int(s_info.get("slabs", 0)),
+                         "upload_gb_per_s": round(s_info.get("bytes_uploaded", 0) / (ms_per_step * 1e-3) / 1e9, 1)}}
+           if args.form == "streamed" else {}),
         "load_s": round(t_load, 3),
     }
     ctx.close()
@@ -506,6 +576,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="skip the launch autotuner (default configuration)")
     ap.add_argument("--store", default="", choices=["", "f32", "bf16"], help="override the workload's storage")
+    ap.add_argument("--form", default="batch", choices=["batch", "streamed", "labelled", "vector"],
+                    help="form of the march (see the module docstring)")
+    ap.add_argument("--slab", type=int, default=64, help="z cells per slab of the streamed form")
     ap.add_argument("--per-image", action="store_true",
                     help="plain per-image march: one render call per view, default layout, no tuning")
     ap.add_argument("--tune-layout", action="store_true", help="(default) also autotune the volume's layout")

@@ -268,7 +268,7 @@ int gbd_render_batch_noalloc(gbd_ctx *ctx, gbd_volume vol, const gbd_view *views
  *  - the images agree with gbd_render_batch of the whole volume to float32
  *    rounding (each slab restarts the ray's anchor; within 2e-5 relative);
  *  - device memory: two slab buffers (records of the slab's snapshots, its
- *    tables, one snapshot of raw fields), checked against the budget
+ *    tables, the slab's raw fields), checked against the budget
  *    (GBD_ERR_BUDGET);
  *  - the call returns when the images are complete; info receives the slabs
  *    marched and the bytes uploaded against the bytes of the whole series. */

@@ -68,7 +68,7 @@ void epoch_span(const gbd_grid &g, const gbd_view &v, const double lo[3], const 
 
 struct SlabBuffer {
     Volume vol;                  // the slab as a volume of its own (device records and tables)
-    char *stage = nullptr;       // one epoch of raw fields of a slab
+    char *stage = nullptr;       // raw fields of a slab: j' of every kept snapshot, then beta
     std::vector<int32_t> tab;    // host copy of the layout tables being uploaded
     cudaEvent_t packed = nullptr, rendered = nullptr;
     bool used = false;
@@ -149,7 +149,7 @@ extern "C" int gbd_render_streamed(gbd_ctx *ctx, const gbd_grid *grid, const gbd
     long long stride = 0;
     const size_t rec_bytes = volume_bytes(f->store, cells, std::max(max_epochs, 1), 0, &stride);
     const size_t tab_bytes = tab.size() * sizeof(int32_t);
-    const size_t stage_bytes = layer * slab * esz * 4;
+    const size_t stage_bytes = layer * slab * esz * 4 * static_cast<size_t>(std::max(max_epochs, 1));
     const uint64_t need = 2 * (rec_bytes + tab_bytes + stage_bytes);
     if (ctx->used + need > ctx->budget)
         return fail(GBD_ERR_BUDGET, "two slab buffers need %llu bytes; %llu of %llu budget in use",
@@ -210,16 +210,24 @@ extern "C" int gbd_render_streamed(gbd_ctx *ctx, const gbd_grid *grid, const gbd
                                 cs);
         const size_t ncell = layer * g.n[2];
         const size_t scount = layer * nz;
+        // The slab's part of each kept snapshot is one contiguous run of the
+        // host arrays, the runs a snapshot apart: one 2D copy per field moves
+        // them all at the link's rate.  The staging buffer is reused two slabs
+        // later, after this slab's packs on the same stream.
+        const size_t jrun = scount * esz, vrun = scount * esz * 3;
+        char *jst = b.stage, *vst = b.stage + jrun * ne;
+        if (e == cudaSuccess)
+            e = cudaMemcpy2DAsync(jst, jrun, static_cast<const char *>(f->j) + (m0[k] * ncell + z0 * layer) * esz,
+                                  ncell * esz, jrun, ne, cudaMemcpyHostToDevice, cs);
+        if (e == cudaSuccess)
+            e = cudaMemcpy2DAsync(vst, vrun,
+                                  static_cast<const char *>(f->vel) + (m0[k] * ncell + z0 * layer) * esz * 3,
+                                  ncell * esz * 3, vrun, ne, cudaMemcpyHostToDevice, cs);
         for (int m = m0[k]; m <= m1[k] && e == cudaSuccess; ++m) {
-            const char *jsrc = static_cast<const char *>(f->j) + (m * ncell + z0 * layer) * esz;
-            const char *vsrc = static_cast<const char *>(f->vel) + (m * ncell + z0 * layer) * esz * 3;
-            e = cudaMemcpyAsync(b.stage, jsrc, scount * esz, cudaMemcpyHostToDevice, cs);
-            if (e == cudaSuccess)
-                e = cudaMemcpyAsync(b.stage + scount * esz, vsrc, scount * esz * 3, cudaMemcpyHostToDevice, cs);
             PackArgs pa;
             std::memset(&pa, 0, sizeof(pa));
-            pa.j = b.stage;
-            pa.vel = b.stage + scount * esz;
+            pa.j = jst + (m - m0[k]) * jrun;
+            pa.vel = vst + (m - m0[k]) * vrun;
             pa.dtype_in = f->dtype_in;
             pa.store = f->store;
             for (int i = 0; i < 3; ++i) pa.n[i] = sv.grid.n[i];
@@ -230,8 +238,6 @@ extern "C" int gbd_render_streamed(gbd_ctx *ctx, const gbd_grid *grid, const gbd
             pa.paired = 0;
             pa.bad = bad;
             if (e == cudaSuccess) e = launch_pack(pa, cs);
-            // the staging buffer takes the next epoch once this one is packed
-            if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
             uploaded += scount * esz * 4;
         }
         if (e == cudaSuccess) e = cudaEventRecord(b.packed, cs);
