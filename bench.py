@@ -251,7 +251,19 @@ def run_gpu(args, rank: int, world: int):
                                        slab=args.slab, flexload=True, launch=s_launch, stream=stream)
             s_info.update(s)
         step()
-        form_note = {"form": "streamed", "slab": args.slab, "flexload": True}
+        # the host link's measured rate: a 1 GiB pinned host-to-device copy
+        probe_h = torch.empty(1 << 30, dtype=torch.uint8, pin_memory=True)
+        probe_d = torch.empty(1 << 30, dtype=torch.uint8, device=f"cuda:{dev}")
+        probe_d.copy_(probe_h, non_blocking=True)
+        torch.cuda.synchronize()
+        t_p = time.perf_counter()
+        for _ in range(4):
+            probe_d.copy_(probe_h, non_blocking=True)
+        torch.cuda.synchronize()
+        h2d_peak = 4 * (1 << 30) / (time.perf_counter() - t_p) / 1e9
+        del probe_h, probe_d
+        form_note = {"form": "streamed", "slab": args.slab, "flexload": True,
+                     "h2d_peak_gb_per_s": round(h2d_peak, 1)}
     elif args.form == "labelled":
         g = wl["grid"]
         cut = g.n[0] // 2
@@ -384,7 +396,9 @@ def run_gpu(args, rank: int, world: int):
         **({"form": form_note} if form_note else {}),
         **({"streamed": {"bytes_uploaded_per_step": int(s_info.get("bytes_uploaded", 0)),
                          "bytes_of_series": int(s_info.get("bytes_total", 0)), "slabs": int(s_info.get("slabs", 0)),
-                         "upload_gb_per_s": round(s_info.get("bytes_uploaded", 0) / (ms_per_step * 1e-3) / 1e9, 1)}}
+                         "upload_gb_per_s": round(s_info.get("bytes_uploaded", 0) / (ms_per_step * 1e-3) / 1e9, 1),
+                         "link_frac": round(s_info.get("bytes_uploaded", 0) / (ms_per_step * 1e-3) / 1e9
+                                            / max(form_note.get("h2d_peak_gb_per_s", 1.0), 1e-9), 3)}}
            if args.form == "streamed" else {}),
         "load_s": round(t_load, 3),
     }

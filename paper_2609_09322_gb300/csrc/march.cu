@@ -383,7 +383,6 @@ __device__ __forceinline__ void march_ray(const VolDev &vol, const ViewDev &V, c
             }
         }
     }
-    const long long u_lo = -(1LL << 32);  // u = -1
     const int Mm1 = vol.M - 1;
 
     BoostConsts bc;
@@ -431,7 +430,8 @@ __device__ __forceinline__ void march_ray(const VolDev &vol, const ViewDev &V, c
                 const int mb = static_cast<int>(um >> 32);
                 const uint32_t frac = static_cast<uint32_t>(um);
                 const float w = static_cast<float>(frac) * 2.3283064365386963e-10f;
-                const bool inside = um > u_lo && mb <= Mm1;
+                // -1 <= m_bar <= M - 1 (at u = -1 exactly both weights vanish below)
+                const bool inside = static_cast<unsigned>(mb + 1) <= static_cast<unsigned>(Mm1 + 1);
                 if (ds > 0.f && inside) {
                     has_lo[d] = mb >= 0;
                     has_hi[d] = (mb < Mm1) && (frac != 0u);
@@ -468,9 +468,10 @@ __device__ __forceinline__ void march_ray(const VolDev &vol, const ViewDev &V, c
                 }
                 s_cur = s_exit;
                 u_cur = u_exit;
-                // Past the last time that reaches a snapshot, or out of the
-                // box: nothing further along the ray can contribute.
-                alive = u_exit > u_lo && (ax[0].o | ax[1].o | ax[2].o) >= 0;
+                // Past the last time that reaches a snapshot (u < -1: the high
+                // word below -1; at u = -1 exactly one more empty step), or out
+                // of the box: nothing further along the ray can contribute.
+                alive = static_cast<int>(u_exit >> 32) >= -1 && (ax[0].o | ax[1].o | ax[2].o) >= 0;
             }
         }
         typename Rec::T rlo[DEPTH], rhi[DEPTH];
