@@ -905,6 +905,10 @@ int gbd_destroy(gbd_ctx *ctx)
         if (ctx->err_word) cudaFree(ctx->err_word);
         if (ctx->load_stream) cudaStreamDestroy(ctx->load_stream);
         if (ctx->capture_stream) cudaStreamDestroy(ctx->capture_stream);
+        for (int k = 0; k < 4; ++k) {
+            if (ctx->aux[k]) cudaStreamDestroy(ctx->aux[k]);
+            if (ctx->aux_done[k]) cudaEventDestroy(ctx->aux_done[k]);
+        }
     }
     delete ctx;
     return GBD_OK;

@@ -61,6 +61,8 @@ struct gbd_ctx {
     gbd_volume next_id = 0;
     cudaStream_t load_stream = nullptr;
     cudaStream_t capture_stream = nullptr;
+    cudaStream_t aux[4] = {};         // side streams of multi-volume renders (created on first use)
+    cudaEvent_t aux_done[4] = {};
     int *err_word = nullptr;          // bounds-check word of checked builds
     gbd::GraphCache *graphs = nullptr;
     gbd::Server *server = nullptr;

@@ -161,6 +161,8 @@ extern "C" int gbd_render_streamed(gbd_ctx *ctx, const gbd_grid *grid, const gbd
     SlabBuffer buf[2];
     int *bad = nullptr;
     cudaError_t e = cudaSuccess;
+    if (!ctx->aux[0]) e = cudaStreamCreateWithFlags(&ctx->aux[0], cudaStreamNonBlocking);
+    if (e == cudaSuccess && !ctx->aux_done[0]) e = cudaEventCreateWithFlags(&ctx->aux_done[0], cudaEventDisableTiming);
     for (auto &b : buf) {
         if (e == cudaSuccess) e = cudaMalloc(&b.vol.rec, rec_bytes);
         if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void **>(&b.vol.axis_off), tab_bytes);
@@ -211,18 +213,24 @@ extern "C" int gbd_render_streamed(gbd_ctx *ctx, const gbd_grid *grid, const gbd
         const size_t ncell = layer * g.n[2];
         const size_t scount = layer * nz;
         // The slab's part of each kept snapshot is one contiguous run of the
-        // host arrays, the runs a snapshot apart: one 2D copy per field moves
-        // them all at the link's rate.  The staging buffer is reused two slabs
-        // later, after this slab's packs on the same stream.
+        // host arrays: one copy per run, j' on the load stream and beta on a
+        // side stream, so both copy engines work; the packs wait for both.
+        // The staging buffer is reused two slabs later, after this slab's
+        // packs on the load stream.
         const size_t jrun = scount * esz, vrun = scount * esz * 3;
         char *jst = b.stage, *vst = b.stage + jrun * ne;
-        if (e == cudaSuccess)
-            e = cudaMemcpy2DAsync(jst, jrun, static_cast<const char *>(f->j) + (m0[k] * ncell + z0 * layer) * esz,
-                                  ncell * esz, jrun, ne, cudaMemcpyHostToDevice, cs);
-        if (e == cudaSuccess)
-            e = cudaMemcpy2DAsync(vst, vrun,
-                                  static_cast<const char *>(f->vel) + (m0[k] * ncell + z0 * layer) * esz * 3,
-                                  ncell * esz * 3, vrun, ne, cudaMemcpyHostToDevice, cs);
+        cudaStream_t vs = ctx->aux[0];
+        if (b.used && e == cudaSuccess) e = cudaStreamWaitEvent(vs, b.rendered, 0);
+        for (int m = m0[k]; m <= m1[k] && e == cudaSuccess; ++m) {
+            e = cudaMemcpyAsync(jst + (m - m0[k]) * jrun, static_cast<const char *>(f->j) + (m * ncell + z0 * layer) * esz,
+                                jrun, cudaMemcpyHostToDevice, cs);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(vst + (m - m0[k]) * vrun,
+                                    static_cast<const char *>(f->vel) + (m * ncell + z0 * layer) * esz * 3, vrun,
+                                    cudaMemcpyHostToDevice, vs);
+        }
+        if (e == cudaSuccess) e = cudaEventRecord(ctx->aux_done[0], vs);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, ctx->aux_done[0], 0);
         for (int m = m0[k]; m <= m1[k] && e == cudaSuccess; ++m) {
             PackArgs pa;
             std::memset(&pa, 0, sizeof(pa));
@@ -259,7 +267,9 @@ extern "C" int gbd_render_streamed(gbd_ctx *ctx, const gbd_grid *grid, const gbd
         ++slabs_done;
     }
     int h_bad = 0;
-    cudaError_t es = cudaStreamSynchronize(cs);
+    cudaError_t es = cudaStreamSynchronize(ctx->aux[0]);
+    if (e == cudaSuccess) e = es;
+    es = cudaStreamSynchronize(cs);
     if (e == cudaSuccess) e = es;
     es = cudaStreamSynchronize(rs);
     if (e == cudaSuccess) e = es;
@@ -281,8 +291,10 @@ extern "C" int gbd_render_streamed(gbd_ctx *ctx, const gbd_grid *grid, const gbd
 // ------------------------------------------------------------ labelled mode
 // Several resident volumes, each a sub-domain with its own grid (origin, cell
 // size, dimensions, snapshot times): a ray's sum over their union is the sum
-// of its sums over each, marched one after another and added into the images
-// in the order given.
+// of its sums over each.  The sub-domains are marched side by side on the
+// context's side streams, each into an image of its own, and the images are
+// added in the order given (the same sums as adding them one by one); with
+// sample counts they are marched one after another, adding into the images.
 extern "C" int gbd_render_labelled(gbd_ctx *ctx, const gbd_volume *vols, int32_t n_vols, const gbd_view *views,
                                    int32_t n, const gbd_image_spec *spec, const gbd_launch *launch, void *stream)
 {
@@ -330,19 +342,61 @@ extern "C" int gbd_render_labelled(gbd_ctx *ctx, const gbd_volume *vols, int32_t
     auto args = std::make_unique<MarchArgs>();
     std::vector<ViewDev> hv(static_cast<size_t>(n));
     int launches = 0;
+    const bool side_by_side = n_vols > 1 && !spec->samples;
+    float *parts = nullptr;
+    cudaEvent_t start = nullptr;
+    if (side_by_side) {
+        for (int s = 0; s < 4 && e == cudaSuccess; ++s) {
+            if (!ctx->aux[s]) e = cudaStreamCreateWithFlags(&ctx->aux[s], cudaStreamNonBlocking);
+            if (e == cudaSuccess && !ctx->aux_done[s])
+                e = cudaEventCreateWithFlags(&ctx->aux_done[s], cudaEventDisableTiming);
+        }
+        if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void **>(&parts), pix * sizeof(float) * n_vols, st);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&start, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventRecord(start, st);
+    }
     for (int k = 0; k < n_vols && e == cudaSuccess && rc == GBD_OK; ++k) {
         for (int v = 0; v < n && rc == GBD_OK; ++v)
             rc = make_view(*vs[k], views[v], spec->width, spec->height, spec->fov_u, spec->fov_v, hv[v]);
         if (rc != GBD_OK) break;
         const std::vector<double> work = view_works(*vs[k], hv, spec->width, spec->height);
         int *q = reinterpret_cast<int *>(queue + k * qbytes);
+        cudaStream_t ks = side_by_side ? ctx->aux[k % 4] : st;
+        if (side_by_side) e = cudaStreamWaitEvent(ks, start, 0);
         for (int c = 0; c < march_chunks(n) && e == cudaSuccess; ++c) {
-            fill_args(*args, *vs[k], hv.data(), n, c, *spec, spec->out, spec->samples, q, cfg, ctx->err_word);
-            args->accumulate = 1;
-            e = launch_march(*args, cfg, ctx->num_sms, work.data() + static_cast<size_t>(c) * kViewsPerLaunch, st);
+            if (side_by_side) {
+                fill_args(*args, *vs[k], hv.data(), n, c, *spec, parts + pix * k, nullptr, q, cfg, ctx->err_word);
+            } else {
+                fill_args(*args, *vs[k], hv.data(), n, c, *spec, spec->out, spec->samples, q, cfg, ctx->err_word);
+                args->accumulate = 1;
+            }
+            e = launch_march(*args, cfg, ctx->num_sms, work.data() + static_cast<size_t>(c) * kViewsPerLaunch, ks);
+            ++launches;
+        }
+        // side streams: the caller's stream waits for each sub-domain
+        if (side_by_side && e == cudaSuccess) e = cudaEventRecord(ctx->aux_done[k % 4], ks);
+        if (side_by_side && e == cudaSuccess) e = cudaStreamWaitEvent(st, ctx->aux_done[k % 4], 0);
+    }
+    if (side_by_side && e == cudaSuccess && rc == GBD_OK) {
+        // add the sub-domains' images in order (prefactors already applied)
+        auto r = std::make_unique<ReduceArgs>();
+        const long long per = static_cast<long long>(spec->width) * spec->height;
+        for (int first = 0; first < n && e == cudaSuccess; first += kViewsPerRegionLaunch) {
+            const int cnt = std::min(kViewsPerRegionLaunch, n - first);
+            std::memset(r.get(), 0, sizeof(ReduceArgs));
+            r->out = spec->out + first * per;
+            r->partial = parts + first * per;
+            r->slot_stride = static_cast<long long>(pix);
+            r->pix_per_view = per;
+            r->n_views = cnt;
+            r->n_slots = n_vols;
+            for (int v = 0; v < cnt; ++v) r->prefactor[v] = 1.0f;
+            e = launch_reduce(*r, st);
             ++launches;
         }
     }
+    if (parts) cudaFreeAsync(parts, st);
+    if (start) cudaEventDestroy(start);
     cudaError_t ef = cudaFreeAsync(queue, st);
     if (rc != GBD_OK) return rc;
     if (e != cudaSuccess) return cuda_fail(e, "labelled render");
