@@ -358,6 +358,10 @@ def run_gpu(args, rank: int, world: int):
 
     rec = RECORD_BYTES[wl["store"]]
     bytes_per_sample = rec * (2 if wl["lookback"] else 1) + extra_bytes_per_sample
+    # compulsory floor: the distinct records a step reads, each once (outside the timed region)
+    compulsory = None
+    if args.form == "batch":
+        compulsory = ctx.touched_records(vol, views) * rec
     alg_bytes = samples_per_step * bytes_per_sample
     kernel_ms = statistics.median(per_step)
     achieved = alg_bytes / (kernel_ms * 1e-3) / 1e9
@@ -387,6 +391,7 @@ def run_gpu(args, rank: int, world: int):
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                      "frac": round(achieved / peak, 4), "traffic": traffic,
                      "peak_source": f"{peak_kind} hbm_gbs", "bytes_per_sample": bytes_per_sample,
+                     "compulsory_bytes_per_step": compulsory,
                      "kernel_ms_median": round(kernel_ms, 4)},
         "e2e": {"value": round(world * samples_per_step / e2e_s / 1e9, 4), "unit": UNIT,
                 "h2d_bytes_per_step": view_bytes, "d2h_bytes_per_step": img_bytes,

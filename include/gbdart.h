@@ -313,6 +313,15 @@ int gbd_load_channels(gbd_ctx *ctx, gbd_volume vol, const void *channels, int32_
 int gbd_render_vector(gbd_ctx *ctx, gbd_volume vol, const gbd_view *views, int32_t n, const gbd_image_spec *spec,
                       const gbd_launch *launch, void *stream);
 
+/* Memory analysis: *records receives the number of distinct (cell, snapshot)
+ * records the samples of a batch render of these views read (each counted
+ * once however many rays or views read it).  Times the record size, it is
+ * the compulsory floor of the render's memory traffic.  The march runs as for
+ * gbd_render_batch but marks a bitmap of one bit per cell and snapshot (held
+ * during the call) instead of reading records; spec->out is not used. */
+int gbd_touched_records(gbd_ctx *ctx, gbd_volume vol, const gbd_view *views, int32_t n,
+                        const gbd_image_spec *spec, uint64_t *records);
+
 /* Number of kernels the last successful render call of this thread
  * launched (graph replays count their kernels). */
 int32_t gbd_last_launch_count(void);

@@ -1150,6 +1150,49 @@ int gbd_load_channels(gbd_ctx *ctx, gbd_volume vid, const void *chans, int32_t n
     return GBD_OK;
 }
 
+int gbd_touched_records(gbd_ctx *ctx, gbd_volume vid, const gbd_view *views, int32_t n,
+                        const gbd_image_spec *spec, uint64_t *records)
+{
+    if (!ctx || !views || !spec || !records) return fail(GBD_ERR_INVALID, "NULL argument");
+    if (n < 1 || n > (1 << 20)) return fail(GBD_ERR_INVALID, "batch size must be in [1, 2^20]");
+    if (spec->width < 1 || spec->height < 1 || spec->width > 16384 || spec->height > 16384)
+        return fail(GBD_ERR_INVALID, "image: width/height must be in [1, 16384]");
+    *records = 0;
+    std::lock_guard<std::mutex> lock(ctx->mu);
+    Volume *vol = ctx->find(vid);
+    if (!vol) return fail(GBD_ERR_NOTFOUND, "unknown volume %llu", static_cast<unsigned long long>(vid));
+    DeviceGuard guard(ctx->device);
+    int rc;
+    std::vector<ViewDev> hv(static_cast<size_t>(n));
+    for (int k = 0; k < n; ++k)
+        if ((rc = make_view(*vol, views[k], spec->width, spec->height, spec->fov_u, spec->fov_v, hv[k]))) return rc;
+    std::vector<int32_t> tab;
+    long long cells = 0;
+    build_layout(vol->grid.n, vol->brick, vol->super_brick, tab, cells, vol->morton_cells);
+    const size_t words = (static_cast<size_t>(cells) * vol->grid.n_epochs + 31) / 32;
+    uint32_t *bits = nullptr;
+    cudaStream_t st = ctx->load_stream;
+    cudaError_t e = cudaMalloc(reinterpret_cast<void **>(&bits), words * 4);
+    if (e == cudaSuccess) e = cudaMemsetAsync(bits, 0, words * 4, st);
+    LaunchCfg cfg = resolve_launch(nullptr);
+    auto a = std::make_unique<MarchArgs>();
+    gbd_image_spec s = *spec;
+    s.out = nullptr;  // the analysis writes no image
+    for (int c = 0; c < march_chunks(n) && e == cudaSuccess; ++c) {
+        fill_args(*a, *vol, hv.data(), n, c, s, reinterpret_cast<float *>(bits), nullptr, nullptr, cfg, ctx->err_word);
+        e = launch_touch(*a, bits, cells, cfg, ctx->num_sms, st);
+    }
+    std::vector<uint32_t> host(words);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(host.data(), bits, words * 4, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (bits) cudaFree(bits);
+    if (e != cudaSuccess) return cuda_fail(e, "touched records");
+    uint64_t count = 0;
+    for (uint32_t w : host) count += static_cast<uint64_t>(__builtin_popcount(w));
+    *records = count;
+    return GBD_OK;
+}
+
 int gbd_render_vector(gbd_ctx *ctx, gbd_volume vid, const gbd_view *views, int32_t n, const gbd_image_spec *spec,
                       const gbd_launch *launch, void *stream)
 {

@@ -198,6 +198,10 @@ struct KernelLaunch {
 cudaError_t plan_march(MarchArgs &a, const LaunchCfg &cfg, int num_sms, const double *work, KernelLaunch &k);
 cudaError_t launch_march(MarchArgs &a, const LaunchCfg &cfg, int num_sms, const double *work, cudaStream_t stream);
 cudaError_t launch_wave(const WaveArgs &a, const LaunchCfg &cfg, cudaStream_t stream);
+// Memory analysis: sets bit m * cells + cell of `bits` for every record the
+// views' samples read (a non-persistent launch planned like the march).
+cudaError_t launch_touch(MarchArgs &a, uint32_t *bits, long long cells, const LaunchCfg &cfg, int num_sms,
+                         cudaStream_t stream);
 // Vector render: n_chan (1 or 3) extra channels besides j'; image v's
 // component c at out + v * img_stride + c * width * height.
 cudaError_t launch_vector(MarchArgs &a, int n_chan, const LaunchCfg &cfg, int num_sms, const double *work,

@@ -253,16 +253,21 @@ __device__ __forceinline__ RayBox grid_box(const VolDev &vol, const ViewDev &V)
 // channels sharing its velocity; each is summed with the same weights and
 // Doppler factors as j' (Eq. 19 per channel) into component c + 1 of the
 // pixel, at out_img + (c + 1) * width * height.
+//
+// TOUCH (memory analysis, not a render): instead of reading the two records
+// of a sample, set the bits of (snapshot, cell) in the bitmap `touch`, whose
+// bit m * cell_stride + cell stands for that record.
 struct ChanPtrs {
     const float *chan;
     long long comp_stride, cell_stride;
+    uint32_t *touch;
 };
 
-template <int STORE, int DEPTH, bool PAIRED, bool SMEM, bool PARTIAL = false, int NCH = 0>
+template <int STORE, int DEPTH, bool PAIRED, bool SMEM, bool PARTIAL = false, int NCH = 0, bool TOUCH = false>
 __device__ __forceinline__ void march_ray(const VolDev &vol, const ViewDev &V, const RayBox &B, int p, int q,
                                           int width, int height, float *out_img, uint32_t *cnt_img, int *err_word,
                                           const int32_t *__restrict__ tab, bool accumulate = false,
-                                          const ChanPtrs ch = ChanPtrs{nullptr, 0, 0})
+                                          const ChanPtrs ch = ChanPtrs{nullptr, 0, 0, nullptr})
 {
     using Rec = Record<STORE>;
     const bool in_image = (p < width) && (q < height);
@@ -446,7 +451,7 @@ __device__ __forceinline__ void march_ray(const VolDev &vol, const ViewDev &V, c
                     // mb + 1 side by side in block mb + 1
                     off[d] = PAIRED ? static_cast<long long>(mb + 1) * es + 2LL * sum
                                     : static_cast<long long>(mb) * es + sum;
-                    if constexpr (NCH > 0) coff[d] = static_cast<long long>(mb) * ch.cell_stride + sum;
+                    if constexpr (NCH > 0 || TOUCH) coff[d] = static_cast<long long>(mb) * ch.cell_stride + sum;
                     wgt[d] = w;
                     dsv[d] = ds;
                 }
@@ -477,7 +482,15 @@ __device__ __forceinline__ void march_ray(const VolDev &vol, const ViewDev &V, c
         typename Rec::T rlo[DEPTH], rhi[DEPTH];
 #pragma unroll
         for (int d = 0; d < DEPTH; ++d) {
-            if (PAIRED) {
+            if constexpr (TOUCH) {
+                rlo[d] = Rec::zero();
+                rhi[d] = Rec::zero();
+                if (has_lo[d]) atomicOr(ch.touch + (coff[d] >> 5), 1u << (coff[d] & 31));
+                if (has_hi[d]) {
+                    const long long i = coff[d] + ch.cell_stride;
+                    atomicOr(ch.touch + (i >> 5), 1u << (i & 31));
+                }
+            } else if (PAIRED) {
                 rlo[d] = Rec::zero();
                 rhi[d] = Rec::zero();
                 if (has_lo[d] || has_hi[d]) Rec::load_pair(recs, off[d], rlo[d], rhi[d]);
@@ -534,7 +547,7 @@ __device__ __forceinline__ void march_ray(const VolDev &vol, const ViewDev &V, c
         }
     }
 
-    if (in_image) {
+    if (in_image && !TOUCH) {
         const long long pix = static_cast<long long>(q) * width + p;
         if (PARTIAL) {
             if (count > 0u) atomicAdd(out_img + pix, acc);
@@ -646,6 +659,38 @@ __global__ void __launch_bounds__(256, 1) vector_kernel(const __grid_constant__ 
                                                        a.error_word, s_tab, false, ch);
         if (!a.persistent) break;
     }
+}
+
+// Memory analysis: marks every (snapshot, cell) record the views' samples
+// read (one packet per warp, no persistent queue).
+template <int STORE, bool PAIRED>
+__global__ void __launch_bounds__(256, 1) touch_kernel(const __grid_constant__ MarchArgs a, uint32_t *bits,
+                                                        long long cells)
+{
+    extern __shared__ int32_t s_tab[];
+    const int ntab = march_table_entries(a.vol.n);
+    for (int i = threadIdx.x; i < ntab; i += blockDim.x) s_tab[i] = a.vol.mtab[i];
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int wpc = blockDim.x >> 5;
+    const int b = static_cast<int>(blockIdx.x);
+    int vi = 0, hi = a.n_views - 1;
+    while (vi < hi) {
+        const int mid = (vi + hi + 1) >> 1;
+        if (a.cta_begin[mid] <= b) vi = mid;
+        else hi = mid - 1;
+    }
+    const ViewDev &V = a.views[vi];
+    const RayBox box = grid_box(a.vol, V);
+    const int tile = (b - a.cta_begin[vi]) * wpc + warp;
+    if (tile >= a.tiles_x * a.tiles_y) return;
+    const int p = (tile % a.tiles_x) * a.packet_w + lane % a.packet_w;
+    const int q = (tile / a.tiles_x) * a.packet_h + lane / a.packet_w;
+    float *out = a.out + static_cast<long long>(vi) * a.width * a.height;
+    const ChanPtrs ch{nullptr, 0, cells, bits};
+    march_ray<STORE, 1, PAIRED, true, false, 0, true>(a.vol, V, box, p, q, a.width, a.height, out, nullptr,
+                                                       a.error_word, s_tab, false, ch);
 }
 
 // Serving: one launch over the tiles of many requests, each with its own
@@ -891,6 +936,27 @@ cudaError_t launch_vector(MarchArgs &a, int n_chan, const LaunchCfg &cfg, int nu
         if (e != cudaSuccess) return e;
     }
     void *params[] = {&a};
+    return cudaLaunchKernel(k, L.grid, L.block, params, L.smem, stream);
+}
+
+cudaError_t launch_touch(MarchArgs &a, uint32_t *bits, long long cells, const LaunchCfg &cfg, int num_sms,
+                         cudaStream_t stream)
+{
+    void *k = a.vol.store == GBD_STORE_F32
+                  ? (a.vol.paired ? reinterpret_cast<void *>(&touch_kernel<GBD_STORE_F32, true>)
+                                  : reinterpret_cast<void *>(&touch_kernel<GBD_STORE_F32, false>))
+                  : (a.vol.paired ? reinterpret_cast<void *>(&touch_kernel<GBD_STORE_BF16_F16U, true>)
+                                  : reinterpret_cast<void *>(&touch_kernel<GBD_STORE_BF16_F16U, false>));
+    // one packet per warp: the grid covers every tile
+    a.persistent = 0;
+    KernelLaunch L;
+    cudaError_t e = plan_march(a, cfg, num_sms, nullptr, L);
+    if (e != cudaSuccess) return e;
+    if (L.smem > 48 * 1024) {
+        e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, L.smem);
+        if (e != cudaSuccess) return e;
+    }
+    void *params[] = {&a, &bits, &cells};
     return cudaLaunchKernel(k, L.grid, L.block, params, L.smem, stream);
 }
 

@@ -132,6 +132,8 @@ _SIGNATURES = {
                            ctypes.c_int32], ctypes.c_int),
     "gbd_render_vector": ([ctypes.c_void_p, ctypes.c_uint64, ctypes.POINTER(CView), ctypes.c_int32,
                            ctypes.POINTER(ImageSpec), ctypes.POINTER(Launch), ctypes.c_void_p], ctypes.c_int),
+    "gbd_touched_records": ([ctypes.c_void_p, ctypes.c_uint64, ctypes.POINTER(CView), ctypes.c_int32,
+                             ctypes.POINTER(ImageSpec), ctypes.POINTER(ctypes.c_uint64)], ctypes.c_int),
     "gbd_serve_start": ([ctypes.c_void_p, ctypes.POINTER(ServeConfig)], ctypes.c_int),
     "gbd_serve_stop": ([ctypes.c_void_p], ctypes.c_int),
     "gbd_submit": ([ctypes.c_void_p, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_uint64)], ctypes.c_int),
@@ -291,6 +293,16 @@ class Context:
         del keep
         _check(self.lib, rc)
         return int(vid.value)
+
+    def touched_records(self, vol: int, views) -> int:
+        """Distinct (cell, snapshot) records a batch render of ``views`` reads."""
+        views = list(views)
+        arr = (CView * len(views))(*[_cview(v) for v in views])
+        spec = self._spec(views[0], None, None)
+        out = ctypes.c_uint64()
+        _check(self.lib, self.lib.gbd_touched_records(self.handle, int(vol), arr, len(views), ctypes.byref(spec),
+                                                      ctypes.byref(out)))
+        return int(out.value)
 
     def load_channels(self, vol: int, channels):
         """Attach extra emissivity channels [K][M][nz][ny][nx] (K = 1 or 3;
