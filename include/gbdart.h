@@ -361,7 +361,9 @@ typedef struct {
     int32_t max_requests_in_flight;  /* request slots (default 1024)                    */
     uint64_t request_budget_bytes;   /* device bytes for running requests; 0 = what the
                                         volumes leave of the context budget              */
-    gbd_launch launch;               /* wave kernel configuration (depth 1 or 2)         */
+    gbd_launch launch;               /* wave kernel configuration (depth 1 or 2); all
+                                        zero: packet 8x4, 4 warps, depth 2, capped
+                                        registers                                 */
 } gbd_serve_config;
 
 typedef struct {

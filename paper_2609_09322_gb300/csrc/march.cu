@@ -696,12 +696,14 @@ __global__ void __launch_bounds__(256, 1) touch_kernel(const __grid_constant__ M
 // Serving: one launch over the tiles of many requests, each with its own
 // volume (float32 or bfloat16/float16 records), view and image.  A CTA finds
 // its request by binary search over the requests' first CTAs (uniform across
-// the CTA).  The march tables are read from global memory (they differ per
-// request); every ray runs the same march_ray as the single-volume kernel, so
-// a request's pixels are the same whether it is served alone or in a mix.
+// the CTA) and stages that request's march tables in shared memory (sized for
+// the largest volume of the launch); every ray runs the same march_ray as the
+// single-volume kernel, so a request's pixels are the same whether it is
+// served alone or in a mix.
 template <int DEPTH, int MINB>
 __global__ void __launch_bounds__(256, MINB) wave_kernel(const __grid_constant__ WaveArgs a)
 {
+    extern __shared__ int32_t s_tab[];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const int wpc = blockDim.x >> 5;
@@ -713,28 +715,30 @@ __global__ void __launch_bounds__(256, MINB) wave_kernel(const __grid_constant__
         else hi = mid - 1;
     }
     const ReqDev &R = a.reqs[lo];
+    const int ntab = march_table_entries(R.vol.n);
+    for (int i = threadIdx.x; i < ntab; i += blockDim.x) s_tab[i] = R.vol.mtab[i];
+    __syncthreads();
     const int tile = (b - R.cta_begin) * wpc + warp;
     if (tile >= R.tiles_x * R.tiles_y) return;
     const int tx = tile % R.tiles_x;
     const int ty = tile / R.tiles_x;
     const int p = tx * a.packet_w + lane % a.packet_w;
     const int q = ty * a.packet_h + lane / a.packet_w;
-    const int32_t *tab = R.vol.mtab;
     const RayBox box = grid_box(R.vol, R.view);
     if (R.vol.store == GBD_STORE_F32) {
         if (R.vol.paired)
-            march_ray<GBD_STORE_F32, DEPTH, true, false>(R.vol, R.view, box, p, q, R.width, R.height, R.out, R.samples,
-                                                         a.error_word, tab);
+            march_ray<GBD_STORE_F32, DEPTH, true, true>(R.vol, R.view, box, p, q, R.width, R.height, R.out, R.samples,
+                                                        a.error_word, s_tab);
         else
-            march_ray<GBD_STORE_F32, DEPTH, false, false>(R.vol, R.view, box, p, q, R.width, R.height, R.out, R.samples,
-                                                          a.error_word, tab);
+            march_ray<GBD_STORE_F32, DEPTH, false, true>(R.vol, R.view, box, p, q, R.width, R.height, R.out, R.samples,
+                                                         a.error_word, s_tab);
     } else {
         if (R.vol.paired)
-            march_ray<GBD_STORE_BF16_F16U, DEPTH, true, false>(R.vol, R.view, box, p, q, R.width, R.height, R.out,
-                                                               R.samples, a.error_word, tab);
+            march_ray<GBD_STORE_BF16_F16U, DEPTH, true, true>(R.vol, R.view, box, p, q, R.width, R.height, R.out,
+                                                              R.samples, a.error_word, s_tab);
         else
-            march_ray<GBD_STORE_BF16_F16U, DEPTH, false, false>(R.vol, R.view, box, p, q, R.width, R.height, R.out,
-                                                                R.samples, a.error_word, tab);
+            march_ray<GBD_STORE_BF16_F16U, DEPTH, false, true>(R.vol, R.view, box, p, q, R.width, R.height, R.out,
+                                                               R.samples, a.error_word, s_tab);
     }
 }
 
@@ -913,8 +917,16 @@ cudaError_t launch_wave(const WaveArgs &a, const LaunchCfg &cfg, cudaStream_t st
     void *k = select_wave(cfg.depth, cfg.regcap);
     if (!k) return cudaErrorInvalidValue;
     if (a.total_ctas < 1) return cudaSuccess;
+    // shared memory for the largest march tables of the launch
+    int smem = 0;
+    for (int r = 0; r < a.n_reqs; ++r)
+        smem = std::max(smem, static_cast<int>(sizeof(int32_t)) * march_table_entries(a.reqs[r].vol.n));
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+    }
     void *params[] = {const_cast<WaveArgs *>(&a)};
-    return cudaLaunchKernel(k, dim3(static_cast<unsigned>(a.total_ctas)), dim3(32 * cfg.cta_warps), params, 0,
+    return cudaLaunchKernel(k, dim3(static_cast<unsigned>(a.total_ctas)), dim3(32 * cfg.cta_warps), params, smem,
                             stream);
 }
 

@@ -316,7 +316,14 @@ int serve_start(Ctx &ctx, const gbd_serve_config *c)
         return fail(GBD_ERR_INVALID, "serve: at most 8 waves of at most 4096 requests");
     s->cfg = d;
     LaunchCfg lc = resolve_launch(c ? &d.launch : nullptr);
-    if (!c) lc.depth = 1;
+    const gbd_launch &ul = d.launch;
+    if (ul.packet_w == 0 && ul.packet_h == 0 && ul.cta_warps == 0 && ul.depth == 0 && ul.regcap == 0) {
+        // launch left unset: the shape the tuner picks for batches (small
+        // CTAs, two cells ahead, the capped register budget)
+        lc.cta_warps = 4;
+        lc.depth = 2;
+        lc.regcap = 1;
+    }
     if (lc.depth > 2) lc.depth = 2;
     lc.persistent = 1;
     lc.region = 0;  // waves march whole rays
