@@ -155,7 +155,11 @@ typedef struct {
     int32_t out_on_host;
 } gbd_image_spec;
 
-/* Launch configuration of the march kernels (chosen by gbd_tune or given). */
+/* Launch configuration of the march kernels (chosen by gbd_tune or given).
+ * A render called with launch NULL uses the tuned configuration of its class
+ * if gbd_tune has run for it, otherwise packet 8x4, 4 warps, depth 2,
+ * persistent, capped registers, no region schedule.  In a given struct, zero
+ * packet/warps/depth fields take those defaults. */
 typedef struct {
     int32_t packet_w, packet_h;  /* pixels of one warp packet: 8x4, 4x8, 16x2, 32x1 */
     int32_t cta_warps;           /* warps per CTA: 1, 2, 4 or 8                     */

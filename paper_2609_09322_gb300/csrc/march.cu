@@ -619,9 +619,9 @@ __global__ void __launch_bounds__(256, MINB) march_kernel(const __grid_constant_
 }
 
 // Vector renders: march_kernel's work split with NCH extra channels summed
-// along every ray (depth 2, persistent, compiler's register budget).
-template <int STORE, int NCH, bool PAIRED>
-__global__ void __launch_bounds__(256, 1) vector_kernel(const __grid_constant__ MarchArgs a)
+// along every ray (depth 2; MINB as for march_kernel).
+template <int STORE, int NCH, bool PAIRED, int MINB>
+__global__ void __launch_bounds__(256, MINB) vector_kernel(const __grid_constant__ MarchArgs a)
 {
     extern __shared__ int32_t s_tab[];
     const int ntab = march_table_entries(a.vol.n);
@@ -891,16 +891,22 @@ void *select_region(int store, int depth, int capped, int paired)
     return nullptr;
 }
 
-template <int NCH>
+template <int NCH, int MINB>
 void *select_vector_store(int store, int paired)
 {
     if (store == GBD_STORE_F32)
-        return paired ? reinterpret_cast<void *>(&vector_kernel<GBD_STORE_F32, NCH, true>)
-                      : reinterpret_cast<void *>(&vector_kernel<GBD_STORE_F32, NCH, false>);
+        return paired ? reinterpret_cast<void *>(&vector_kernel<GBD_STORE_F32, NCH, true, MINB>)
+                      : reinterpret_cast<void *>(&vector_kernel<GBD_STORE_F32, NCH, false, MINB>);
     if (store == GBD_STORE_BF16_F16U)
-        return paired ? reinterpret_cast<void *>(&vector_kernel<GBD_STORE_BF16_F16U, NCH, true>)
-                      : reinterpret_cast<void *>(&vector_kernel<GBD_STORE_BF16_F16U, NCH, false>);
+        return paired ? reinterpret_cast<void *>(&vector_kernel<GBD_STORE_BF16_F16U, NCH, true, MINB>)
+                      : reinterpret_cast<void *>(&vector_kernel<GBD_STORE_BF16_F16U, NCH, false, MINB>);
     return nullptr;
+}
+
+template <int NCH>
+void *select_vector_cap(int store, int paired, int capped)
+{
+    return capped ? select_vector_store<NCH, 3>(store, paired) : select_vector_store<NCH, 1>(store, paired);
 }
 
 void *select_wave(int depth, int capped)
@@ -933,13 +939,12 @@ cudaError_t launch_wave(const WaveArgs &a, const LaunchCfg &cfg, cudaStream_t st
 cudaError_t launch_vector(MarchArgs &a, int n_chan, const LaunchCfg &cfg, int num_sms, const double *work,
                           cudaStream_t stream)
 {
-    void *k = n_chan == 1 ? select_vector_store<1>(a.vol.store, a.vol.paired)
-                          : (n_chan == 3 ? select_vector_store<3>(a.vol.store, a.vol.paired) : nullptr);
+    void *k = n_chan == 1 ? select_vector_cap<1>(a.vol.store, a.vol.paired, cfg.regcap)
+                          : (n_chan == 3 ? select_vector_cap<3>(a.vol.store, a.vol.paired, cfg.regcap) : nullptr);
     if (!k) return cudaErrorInvalidValue;
     // grid as planned for the scalar kernel of the same configuration
     LaunchCfg c = cfg;
     c.depth = 2;
-    c.regcap = 0;
     KernelLaunch L;
     cudaError_t e = plan_march(a, c, num_sms, work, L);
     if (e != cudaSuccess) return e;
