@@ -619,7 +619,7 @@ __global__ void __launch_bounds__(256, MINB) march_kernel(const __grid_constant_
 }
 
 // Vector renders: march_kernel's work split with NCH extra channels summed
-// along every ray (depth 2; MINB as for march_kernel).
+// along every ray (depth 2, the compiler's register budget).
 template <int STORE, int NCH, bool PAIRED, int MINB>
 __global__ void __launch_bounds__(256, MINB) vector_kernel(const __grid_constant__ MarchArgs a)
 {
@@ -903,11 +903,7 @@ void *select_vector_store(int store, int paired)
     return nullptr;
 }
 
-template <int NCH>
-void *select_vector_cap(int store, int paired, int capped)
-{
-    return capped ? select_vector_store<NCH, 3>(store, paired) : select_vector_store<NCH, 1>(store, paired);
-}
+
 
 void *select_wave(int depth, int capped)
 {
@@ -939,12 +935,15 @@ cudaError_t launch_wave(const WaveArgs &a, const LaunchCfg &cfg, cudaStream_t st
 cudaError_t launch_vector(MarchArgs &a, int n_chan, const LaunchCfg &cfg, int num_sms, const double *work,
                           cudaStream_t stream)
 {
-    void *k = n_chan == 1 ? select_vector_cap<1>(a.vol.store, a.vol.paired, cfg.regcap)
-                          : (n_chan == 3 ? select_vector_cap<3>(a.vol.store, a.vol.paired, cfg.regcap) : nullptr);
+    // the compiler's register budget: capped, the three-channel kernel spills
+    // and runs slower than the extra resident warps gain
+    void *k = n_chan == 1 ? select_vector_store<1, 1>(a.vol.store, a.vol.paired)
+                          : (n_chan == 3 ? select_vector_store<3, 1>(a.vol.store, a.vol.paired) : nullptr);
     if (!k) return cudaErrorInvalidValue;
-    // grid as planned for the scalar kernel of the same configuration
+    // grid as planned for the scalar kernel of the same budget
     LaunchCfg c = cfg;
     c.depth = 2;
+    c.regcap = 0;
     KernelLaunch L;
     cudaError_t e = plan_march(a, c, num_sms, work, L);
     if (e != cudaSuccess) return e;
