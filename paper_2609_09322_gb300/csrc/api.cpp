@@ -652,7 +652,7 @@ static cudaError_t chunk_params(Ctx &ctx, const Volume &vol, const GraphKey &key
     KernelLaunch L;
     cudaError_t e = plan_march(a, key.cfg, ctx.num_sms, work, L);
     if (e != cudaSuccess) return e;
-    std::memset(&kp, 0, sizeof(kp));
+    kp = cudaKernelNodeParams{};
     kp.func = L.func;
     kp.gridDim = L.grid;
     kp.blockDim = L.block;
@@ -939,7 +939,6 @@ int gbd_load_snapshots(gbd_ctx *ctx, const gbd_grid *grid, const gbd_fields *f, 
     vol->morton_cells = f->morton_cells ? 1 : 0;
     if (!build_layout(g.n, B, S, tab, cells, vol->morton_cells) || (vol->paired && 2 * cells >= (1LL << 31)))
         return fail(GBD_ERR_INVALID, "grid too large: one epoch exceeds 2^31 records");
-    const size_t rec_bytes = f->store == GBD_STORE_F32 ? 16 : 8;
     const size_t bytes = volume_bytes(f->store, cells, g.n_epochs, vol->paired, &vol->epoch_stride);
     const size_t tab_bytes = tab.size() * sizeof(int32_t);
     if (ctx->used + bytes + tab_bytes > ctx->budget)

@@ -44,7 +44,7 @@ struct TuneKey {
 };
 
 struct TuneEntry {
-    LaunchCfg cfg{8, 4, 8, 2, 1, 0};
+    LaunchCfg cfg{8, 4, 8, 2, 1, 0, 0};
     int brick = 8, super_brick = 4;
     float ms = 0.f;
 };
