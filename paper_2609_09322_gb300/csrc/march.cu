@@ -202,18 +202,39 @@ struct AxisState {
     int32_t pn;     // table term of the next cell (read ahead)
 };
 
-// Steps one axis of a ray into its next cell: the next crossing is recomputed
-// from the plane count (never accumulated), the epoch coordinate drops by the
-// exact per-plane amount, and the table term of the cell after is read ahead.
+// Steps a ray into its next cell through the face of axis 0, 1 or 2 (x0, x1,
+// else axis 2): that axis's next crossing is recomputed from its plane count
+// (never accumulated), its epoch coordinate drops by the exact per-plane
+// amount, and the table term of the cell after is read ahead.  Every update is
+// a select on the exit axis, so the lanes of a warp never diverge here;
+// recomputing an axis's crossing from an unchanged plane count reproduces it
+// (an axis the ray runs parallel to has of = -3e38 and inv_a = 0, so its
+// crossing stays at 3e38).
 template <bool SMEM>
-__device__ __forceinline__ void step_axis(AxisState &A, float inv_a, long long du, const int32_t *tab)
+__device__ __forceinline__ void step_exit(AxisState (&ax)[3], bool x0, bool x1, float ia0, float ia1, float ia2,
+                                          long long du0, long long du1, long long du2, const int32_t *tab)
 {
-    A.nkf += 1.0f;
-    A.sn = fmaf(A.nkf, inv_a, -A.of);
-    A.un -= du;
-    A.o = A.pn;
-    A.cur += 4u;
-    A.pn = tab_at<SMEM>(tab, A.cur + 4u);
+    const bool x2 = !x0 && !x1;
+    const uint32_t ce = x0 ? ax[0].cur : (x1 ? ax[1].cur : ax[2].cur);
+    const int32_t tn = tab_at<SMEM>(tab, ce + 8u);
+    ax[0].nkf = x0 ? ax[0].nkf + 1.0f : ax[0].nkf;
+    ax[1].nkf = x1 ? ax[1].nkf + 1.0f : ax[1].nkf;
+    ax[2].nkf = x2 ? ax[2].nkf + 1.0f : ax[2].nkf;
+    ax[0].un = x0 ? ax[0].un - du0 : ax[0].un;
+    ax[1].un = x1 ? ax[1].un - du1 : ax[1].un;
+    ax[2].un = x2 ? ax[2].un - du2 : ax[2].un;
+    ax[0].o = x0 ? ax[0].pn : ax[0].o;
+    ax[1].o = x1 ? ax[1].pn : ax[1].o;
+    ax[2].o = x2 ? ax[2].pn : ax[2].o;
+    ax[0].pn = x0 ? tn : ax[0].pn;
+    ax[1].pn = x1 ? tn : ax[1].pn;
+    ax[2].pn = x2 ? tn : ax[2].pn;
+    ax[0].cur = x0 ? ax[0].cur + 4u : ax[0].cur;
+    ax[1].cur = x1 ? ax[1].cur + 4u : ax[1].cur;
+    ax[2].cur = x2 ? ax[2].cur + 4u : ax[2].cur;
+    ax[0].sn = fmaf(ax[0].nkf, ia0, -ax[0].of);
+    ax[1].sn = fmaf(ax[1].nkf, ia1, -ax[1].of);
+    ax[2].sn = fmaf(ax[2].nkf, ia2, -ax[2].of);
 }
 
 // The box a ray is marched through, in the march frame (mirrored axes
@@ -331,6 +352,7 @@ __device__ __forceinline__ void march_ray(const VolDev &vol, const ViewDev &V, c
                 u_cur = A.un + V.du[i];
             }
         } else {
+            A.of = -3.0e38f;     // with inv_a = 0: the crossing stays at 3e38,
             A.sn = 3.0e38f;      // never the nearest face ...
             A.un = LLONG_MIN / 2;  // ... and ends the ray if it ever were
         }
@@ -366,22 +388,12 @@ __device__ __forceinline__ void march_ray(const VolDev &vol, const ViewDev &V, c
             const bool x1 = !x0 && ax[1].sn <= ax[2].sn;
             const float s_exit = x0 ? ax[0].sn : (x1 ? ax[1].sn : ax[2].sn);
             if (s_exit > s_cur) break;
-            if (x0) {
-                step_axis<SMEM>(ax[0], ia0, du0, tab);
+            step_exit<SMEM>(ax, x0, x1, ia0, ia1, ia2, du0, du1, du2, tab);
 #ifdef GBD_CHECKED
-                kc[0] += kd0;
+            kc[0] += x0 ? kd0 : 0;
+            kc[1] += x1 ? kd1 : 0;
+            kc[2] += (!x0 && !x1) ? kd2 : 0;
 #endif
-            } else if (x1) {
-                step_axis<SMEM>(ax[1], ia1, du1, tab);
-#ifdef GBD_CHECKED
-                kc[1] += kd1;
-#endif
-            } else {
-                step_axis<SMEM>(ax[2], ia2, du2, tab);
-#ifdef GBD_CHECKED
-                kc[2] += kd2;
-#endif
-            }
             if ((ax[0].o | ax[1].o | ax[2].o) < 0) {
                 alive = false;
                 break;
@@ -455,22 +467,12 @@ __device__ __forceinline__ void march_ray(const VolDev &vol, const ViewDev &V, c
                     wgt[d] = w;
                     dsv[d] = ds;
                 }
-                if (x0) {
-                    step_axis<SMEM>(ax[0], ia0, du0, tab);
+                step_exit<SMEM>(ax, x0, x1, ia0, ia1, ia2, du0, du1, du2, tab);
 #ifdef GBD_CHECKED
-                    kc[0] += kd0;
+                kc[0] += x0 ? kd0 : 0;
+                kc[1] += x1 ? kd1 : 0;
+                kc[2] += (!x0 && !x1) ? kd2 : 0;
 #endif
-                } else if (x1) {
-                    step_axis<SMEM>(ax[1], ia1, du1, tab);
-#ifdef GBD_CHECKED
-                    kc[1] += kd1;
-#endif
-                } else {
-                    step_axis<SMEM>(ax[2], ia2, du2, tab);
-#ifdef GBD_CHECKED
-                    kc[2] += kd2;
-#endif
-                }
                 s_cur = s_exit;
                 u_cur = u_exit;
                 // Past the last time that reaches a snapshot (u < -1: the high
@@ -510,37 +512,47 @@ __device__ __forceinline__ void march_ray(const VolDev &vol, const ViewDev &V, c
                     chi[d][c] = has_hi[d] ? __ldg(base + ch.cell_stride) : 0.f;
                 }
         }
+        if constexpr (NCH == 0) {
+            // A snapshot that a sample does not read is a zero record (not
+            // loaded, or the zero record beside the first and the last
+            // snapshot of a paired layout), whose boosted value is exactly 0,
+            // so both are evaluated without a branch.  The compensated sum
+            // takes a sample only where it read a snapshot, so a ray's sum
+            // does not depend on how long the other lanes of its warp march.
 #pragma unroll
-        for (int d = 0; d < DEPTH; ++d) {
-            if (has_lo[d] || has_hi[d]) {
-                if constexpr (NCH == 0) {
-                    const float vlo = has_lo[d] ? Rec::boosted(rlo[d], bc) : 0.f;
-                    const float vhi = has_hi[d] ? Rec::boosted(rhi[d], bc) : 0.f;
-                    const float v = fmaf(wgt[d], vhi - vlo, vlo);       // Eq. 8
-                    const float y = fmaf(v, dsv[d], -comp);             // compensated sum
-                    const float t = acc + y;
-                    comp = (t - acc) - y;
-                    acc = t;
-                } else {
-                    // the Doppler factor of each snapshot serves every channel
-                    const float blo = has_lo[d] ? Rec::boost(rlo[d], bc) : 0.f;
-                    const float bhi = has_hi[d] ? Rec::boost(rhi[d], bc) : 0.f;
-                    const float vlo = has_lo[d] ? Rec::emissivity(rlo[d]) * blo : 0.f;
-                    const float vhi = has_hi[d] ? Rec::emissivity(rhi[d]) * bhi : 0.f;
-                    const float v = fmaf(wgt[d], vhi - vlo, vlo);
-                    const float y = fmaf(v, dsv[d], -comp);
-                    const float t = acc + y;
-                    comp = (t - acc) - y;
-                    acc = t;
+            for (int d = 0; d < DEPTH; ++d) {
+                const float vlo = Rec::boosted(rlo[d], bc);
+                const float vhi = Rec::boosted(rhi[d], bc);
+                const float v = fmaf(wgt[d], vhi - vlo, vlo);       // Eq. 8
+                const float y = fmaf(v, dsv[d], -comp);             // compensated sum
+                const float t = acc + y;
+                const bool take = has_lo[d] || has_hi[d];
+                comp = take ? (t - acc) - y : comp;
+                acc = take ? t : acc;
+                count += take ? 1u : 0u;
+            }
+        } else {
+            // vector renders: the Doppler factor of each snapshot serves every channel
 #pragma unroll
-                    for (int c = 0; c < NCH; ++c) {
-                        const float ulo = clo[d][c] * blo, uhi = chi[d][c] * bhi;
-                        const float u = fmaf(wgt[d], uhi - ulo, ulo);
-                        const float yc = fmaf(u, dsv[d], -ccomp[c]);
-                        const float tc = cacc[c] + yc;
-                        ccomp[c] = (tc - cacc[c]) - yc;
-                        cacc[c] = tc;
-                    }
+            for (int d = 0; d < DEPTH; ++d) {
+                if (!(has_lo[d] || has_hi[d])) continue;
+                const float blo = has_lo[d] ? Rec::boost(rlo[d], bc) : 0.f;
+                const float bhi = has_hi[d] ? Rec::boost(rhi[d], bc) : 0.f;
+                const float vlo = has_lo[d] ? Rec::emissivity(rlo[d]) * blo : 0.f;
+                const float vhi = has_hi[d] ? Rec::emissivity(rhi[d]) * bhi : 0.f;
+                const float v = fmaf(wgt[d], vhi - vlo, vlo);
+                const float y = fmaf(v, dsv[d], -comp);
+                const float t = acc + y;
+                comp = (t - acc) - y;
+                acc = t;
+#pragma unroll
+                for (int c = 0; c < NCH; ++c) {
+                    const float ulo = clo[d][c] * blo, uhi = chi[d][c] * bhi;
+                    const float u = fmaf(wgt[d], uhi - ulo, ulo);
+                    const float yc = fmaf(u, dsv[d], -ccomp[c]);
+                    const float tc = cacc[c] + yc;
+                    ccomp[c] = (tc - cacc[c]) - yc;
+                    cacc[c] = tc;
                 }
                 ++count;
             }
