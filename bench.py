@@ -220,8 +220,9 @@ def run_gpu(args, rank: int, world: int):
         vals = [int(x) for x in args.launch.split(",")]
         pw, ph, warps, depth, regcap = vals[:5]
         region = vals[5] if len(vals) > 5 else 0
+        group = vals[6] if len(vals) > 6 else 0
         launch = {"packet": (pw, ph), "cta_warps": warps, "depth": depth, "persistent": 0 if region else 1,
-                  "regcap": regcap, "region": region}
+                  "regcap": regcap, "region": region, "group": group}
         tuned = dict(launch)
     elif not args.no_tune and not args.per_image:
         # autotune the launch (and, with --tune-layout, the volume layout) before timing
@@ -384,7 +385,7 @@ def run_gpu(args, rank: int, world: int):
                    % (info["bytes"] / 1e9), "parallelism": "replicas" if world > 1 else "single GPU",
                    "layout": f"brick {info['brick']}, super-brick {info['super_brick']}"
                              + (", paired snapshots" if info.get("paired") else ""),
-                   "launch": ({k: tuned[k] for k in ("packet", "cta_warps", "depth", "persistent", "regcap", "region") if k in tuned}
+                   "launch": ({k: tuned[k] for k in ("packet", "cta_warps", "depth", "persistent", "regcap", "region", "group") if k in tuned}
                               if tuned else "default")},
         "images_per_s": round(world * n_views / (ms_per_step * 1e-3), 2),
         "rays_per_s": round(world * n_views * views[0].width * views[0].height / (ms_per_step * 1e-3), 1),
@@ -602,7 +603,7 @@ def main():
                     help="plain per-image march: one render call per view, default layout, no tuning")
     ap.add_argument("--tune-layout", action="store_true", help="(default) also autotune the volume's layout")
     ap.add_argument("--no-tune-layout", action="store_true", help="keep the default brick layout")
-    ap.add_argument("--launch", default="", help="fixed launch instead of tuning: packet_w,packet_h,warps,depth,regcap[,region]")
+    ap.add_argument("--launch", default="", help="fixed launch instead of tuning: packet_w,packet_h,warps,depth,regcap[,region[,group]]")
     ap.add_argument("--layout", default="", help="fixed volume layout: brick,super_brick[,paired]")
     args = ap.parse_args()
     if args.warmup < 3:

@@ -158,8 +158,9 @@ typedef struct {
 /* Launch configuration of the march kernels (chosen by gbd_tune or given).
  * A render called with launch NULL uses the tuned configuration of its class
  * if gbd_tune has run for it, otherwise packet 8x4, 4 warps, depth 2,
- * persistent, capped registers, no region schedule.  In a given struct, zero
- * packet/warps/depth fields take those defaults. */
+ * persistent, capped registers, no region schedule, time groups of up to 4.
+ * In a given struct, zero packet/warps/depth/group fields take those
+ * defaults. */
 typedef struct {
     int32_t packet_w, packet_h;  /* pixels of one warp packet: 8x4, 4x8, 16x2, 32x1 */
     int32_t cta_warps;           /* warps per CTA: 1, 2, 4 or 8                     */
@@ -174,6 +175,14 @@ typedef struct {
                                     order.  Images agree with the whole-ray march to
                                     FP32 rounding (a few 1e-6), not bitwise.  Not
                                     used with sample counts; depth 1 or 2.           */
+    int32_t group;               /* batches: time groups.  Consecutive views that
+                                    differ only in observer time (same image plane,
+                                    direction and grid frame; t_obs, and with it the
+                                    window, and nu_ratio free) are marched together,
+                                    up to `group` per ray: one traversal, one sum per
+                                    view.  0 = the default, 4; 1 = every view on its
+                                    own; at most 8.  A grouped view agrees with its
+                                    lone render to FP32 rounding, not bitwise.       */
 } gbd_launch;
 
 /* Description of a resident volume. */

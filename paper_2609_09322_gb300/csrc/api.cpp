@@ -274,8 +274,9 @@ VolDev vol_dev(const Volume &v)
 LaunchCfg resolve_launch(const gbd_launch *l)
 {
     // the default: the shape the autotuner settles on for the workloads here
-    // (8x4 packets, 4-warp CTAs, two cells ahead, capped registers)
-    LaunchCfg c{8, 4, 4, 2, 1, 1, 0};
+    // (8x4 packets, 4-warp CTAs, two cells ahead, capped registers, time
+    // groups of up to four views)
+    LaunchCfg c{8, 4, 4, 2, 1, 1, 0, kGroupDefault};
     if (l) {
         if (l->packet_w > 0) c.packet_w = l->packet_w;
         if (l->packet_h > 0) c.packet_h = l->packet_h;
@@ -284,6 +285,7 @@ LaunchCfg resolve_launch(const gbd_launch *l)
         c.persistent = l->persistent != 0;
         c.regcap = l->regcap != 0;
         c.region = l->region;
+        if (l->group > 0) c.group = l->group;
     }
     return c;
 }
@@ -298,6 +300,7 @@ int check_launch(const LaunchCfg &c)
     if (c.region != 0 && c.region != 16 && c.region != 32 && c.region != 64 && c.region != 128)
         return fail(GBD_ERR_INVALID, "launch: region must be 0, 16, 32, 64 or 128");
     if (c.region != 0 && c.depth > 2) return fail(GBD_ERR_INVALID, "launch: the region schedule takes depth 1 or 2");
+    if (c.group < 1 || c.group > kGroupMax) return fail(GBD_ERR_INVALID, "launch: group must be 0 (default) or 1 .. 8");
     return GBD_OK;
 }
 
@@ -372,6 +375,65 @@ void fill_args(MarchArgs &a, const Volume &vol, const ViewDev *hv, int n, int c,
     a.queue = queue + first;
     a.error_word = err_word;
     std::memcpy(a.views, hv + first, sizeof(ViewDev) * static_cast<size_t>(cnt));
+}
+
+// Two views have the same rays when every per-view constant but the epoch
+// coordinate at the image plane, the window and the prefactor agrees: the
+// same image plane, direction, grid frame, epoch rate per face and boost.
+static bool same_rays(const ViewDev &x, const ViewDev &y)
+{
+    return std::memcmp(x.g0, y.g0, sizeof(x.g0)) == 0 && std::memcmp(x.gu, y.gu, sizeof(x.gu)) == 0 &&
+           std::memcmp(x.gv, y.gv, sizeof(x.gv)) == 0 && std::memcmp(x.du, y.du, sizeof(x.du)) == 0 &&
+           std::memcmp(x.a_hi, y.a_hi, sizeof(x.a_hi)) == 0 && std::memcmp(x.a_lo, y.a_lo, sizeof(x.a_lo)) == 0 &&
+           std::memcmp(x.inv_a, y.inv_a, sizeof(x.inv_a)) == 0 && std::memcmp(x.w_hi, y.w_hi, sizeof(x.w_hi)) == 0 &&
+           std::memcmp(x.w_lo, y.w_lo, sizeof(x.w_lo)) == 0 && std::memcmp(&x.kk_hi, &y.kk_hi, sizeof(float)) == 0 &&
+           std::memcmp(&x.kk_lo, &y.kk_lo, sizeof(float)) == 0 && std::memcmp(x.sh_hi, y.sh_hi, sizeof(x.sh_hi)) == 0 &&
+           std::memcmp(x.sh_lo, y.sh_lo, sizeof(x.sh_lo)) == 0 && std::memcmp(&x.expo, &y.expo, sizeof(float)) == 0 &&
+           x.flags == y.flags;
+}
+
+// Time groups: each run of consecutive views with the same rays becomes
+// ceil(run / gmax) groups of near-equal size.  n_groups stays 0 (every view
+// marched on its own) when gmax < 2 or no run holds two views.
+void group_views(MarchArgs &a, int gmax)
+{
+    a.n_groups = 0;
+    gmax = std::min(gmax, kGroupMax);
+    if (gmax < 2) return;
+    int ng = 0;
+    bool shared = false;
+    for (int v = 0; v < a.n_views;) {
+        int e = v + 1;
+        while (e < a.n_views && same_rays(a.views[v], a.views[e])) ++e;
+        const int len = e - v, parts = (len + gmax - 1) / gmax;
+        for (int k = 0; k < parts; ++k) a.group_first[ng++] = v + len * k / parts;
+        shared = shared || len > 1;
+        v = e;
+    }
+    a.group_first[ng] = a.n_views;
+    if (!shared) return;
+    a.n_groups = ng;
+    int most = 1;
+    for (int g = 0; g < ng; ++g) {
+        const int v0 = a.group_first[g], v1 = a.group_first[g + 1];
+        most = std::max(most, v1 - v0);
+        int ref = v0;
+        float lo = a.views[v0].win_lo, hi = a.views[v0].win_hi;
+        for (int v = v0 + 1; v < v1; ++v) {
+            if (a.views[v].u_obs > a.views[ref].u_obs) ref = v;
+            lo = std::min(lo, a.views[v].win_lo);
+            hi = std::max(hi, a.views[v].win_hi);
+        }
+        a.group_ref[g] = ref;
+        a.group_win[g][0] = lo;
+        a.group_win[g][1] = hi;
+        for (int v = v0; v < v1; ++v) {
+            // both within 1e8 snapshots of zero (make_view), so no overflow
+            a.view_delta[v] = a.views[v].u_obs - a.views[ref].u_obs;
+            a.view_dhi[v] = static_cast<int>(a.view_delta[v] >> 32);
+        }
+    }
+    a.group_size = most <= 4 ? 4 : kGroupMax;
 }
 
 // Bytes of the per-view tile counters of a batch, rounded up to 256.
@@ -564,6 +626,7 @@ int render_direct(Ctx &ctx, const Volume &vol, const std::vector<ViewDev> &hv, c
     for (int c = 0; c < chunks && e == cudaSuccess; ++c) {
         fill_args(*a, vol, hv.data(), n, c, spec, dev_out, spec.out_on_host ? nullptr : spec.samples, queue, cfg,
                   ctx.err_word);
+        group_views(*a, cfg.group);
         e = launch_march(*a, cfg, ctx.num_sms, work.data() + static_cast<size_t>(c) * kViewsPerLaunch, st);
     }
     if (e == cudaSuccess && spec.out_on_host)
@@ -598,6 +661,7 @@ struct GraphEntry {
     cudaGraphExec_t exec = nullptr;
     int region_launches = 0;     // region schedule: kernels per replay (captured; rebuilt for new views)
     std::vector<cudaGraphNode_t> knodes;
+    std::vector<void *> kfuncs;  // the kernel of each node
     std::vector<ViewDev> views;  // the views the kernel nodes hold
     char *d_scratch = nullptr;   // tile counters (+ image when out_on_host)
     cudaEvent_t done = nullptr;
@@ -647,6 +711,7 @@ static cudaError_t chunk_params(Ctx &ctx, const Volume &vol, const GraphKey &key
     float *dev_out = spec.out_on_host ? reinterpret_cast<float *>(g.d_scratch + img_off) : spec.out;
     fill_args(a, vol, hv, key.n, c, spec, dev_out, spec.out_on_host ? nullptr : spec.samples, queue, key.cfg,
               ctx.err_word);
+    group_views(a, key.cfg.group);
     double work[kViewsPerLaunch];
     for (int v = 0; v < a.n_views; ++v) work[v] = view_work(vol, a.views[v], spec.width, spec.height);
     KernelLaunch L;
@@ -660,6 +725,22 @@ static cudaError_t chunk_params(Ctx &ctx, const Volume &vol, const GraphKey &key
     params[0] = &a;
     kp.kernelParams = params;
     return cudaSuccess;
+}
+
+// Whether the views hv would run the same kernel in every node of g (their
+// time groups may call for the grouped kernel where g's views did not).
+static bool same_kernels(Ctx &ctx, const Volume &vol, const GraphKey &key, const gbd_image_spec &spec,
+                         const GraphEntry &g, const std::vector<ViewDev> &hv)
+{
+    auto a = std::make_unique<MarchArgs>();
+    for (size_t c = 0; c < g.knodes.size(); ++c) {
+        cudaKernelNodeParams kp;
+        void *params[1];
+        if (chunk_params(ctx, vol, key, spec, g, hv.data(), static_cast<int>(c), *a, kp, params) != cudaSuccess ||
+            kp.func != g.kfuncs[c])
+            return false;
+    }
+    return true;
 }
 
 // Region schedule: the batch is captured from enqueue_regions.
@@ -726,6 +807,7 @@ static int build_graph(Ctx &ctx, const Volume &vol, const GraphKey &key, const g
         if (e == cudaSuccess) e = cudaGraphAddKernelNode(&kn, g.graph, &mnode, 1, &kp);
         if (e != cudaSuccess) return cuda_fail(e, "batch graph kernel node");
         g.knodes.push_back(kn);
+        g.kfuncs.push_back(kp.func);
     }
     if (spec.out_on_host) {
         cudaGraphNode_t cn = nullptr;
@@ -774,8 +856,10 @@ int render_graph(Ctx &ctx, const Volume &vol, gbd_volume vid, const std::vector<
             return rc;
         }
         slot = std::move(g);
-    } else if (std::memcmp(slot->views.data(), hv.data(), vbytes) != 0 && slot->region_launches > 0) {
-        // region schedule: capture the batch again for the new views
+    } else if (std::memcmp(slot->views.data(), hv.data(), vbytes) != 0 &&
+               (slot->region_launches > 0 || !same_kernels(ctx, vol, key, spec, *slot, hv))) {
+        // region schedule, or new views that group differently (another
+        // kernel): build the batch again for the new views
         if (slot->launched) {
             cudaError_t e = cudaEventSynchronize(slot->done);
             if (e != cudaSuccess) return cuda_fail(e, "wait for previous batch");

@@ -87,6 +87,12 @@ struct ViewDev {
 // are split into several launches.
 constexpr int kViewsPerLaunch = 128;
 
+// Time groups: views of a batch that differ only in observer time are
+// marched together, up to kGroupMax per ray (one sum per member in registers);
+// kGroupDefault when the launch does not say.
+constexpr int kGroupMax = 8;
+constexpr int kGroupDefault = 4;
+
 // One march launch: n_views views of one image geometry.
 struct MarchArgs {
     VolDev vol;
@@ -94,12 +100,19 @@ struct MarchArgs {
     int width, height;
     int packet_w, packet_h;   // packet_w * packet_h == 32
     int tiles_x, tiles_y;     // packets per image row / column
-    int cta_begin[kViewsPerLaunch + 1];  // first CTA of each view, then the total (set by plan_march)
+    int cta_begin[kViewsPerLaunch + 1];  // first CTA of each view (or group), then the total (set by plan_march)
+    int n_groups;             // 0: every view marched on its own; else time groups of consecutive views
+    int group_size;           // time groups: the kernel's member limit (4 or kGroupMax)
+    int group_first[kViewsPerLaunch + 1];  // group g: views group_first[g] .. group_first[g + 1] - 1
+    int group_ref[kViewsPerLaunch];        // the group's reference view: the largest u_obs
+    float group_win[kViewsPerLaunch][2];   // the union of the members' windows
+    long long view_delta[kViewsPerLaunch]; // u_obs of the view minus that of its group's reference, Q31.32
+    int view_dhi[kViewsPerLaunch];         // view_delta >> 32 (whole epochs, rounded down)
     int persistent;           // CTAs loop over their view's tile counter
     int accumulate;           // add to out (and samples) instead of storing
     float *out;               // n_views * width * height floats
     uint32_t *samples;        // optional, same shape
-    int *queue;               // persistent mode: one tile counter per view (zeroed before launch)
+    int *queue;               // persistent mode: one tile counter per view or group (zeroed before launch)
     int *error_word;          // checked builds: first bounds violation code
     // vector renders (vector_kernel): extra emissivity channels of the volume
     const float *chan;        // n_chan channels, each M blocks of chan_cell_stride floats
@@ -181,7 +194,7 @@ static_assert(sizeof(WaveArgs) <= 32764, "wave launch arguments exceed the kerne
 
 // Launch configuration after defaults have been applied.
 struct LaunchCfg {
-    int packet_w, packet_h, cta_warps, depth, persistent, regcap, region;
+    int packet_w, packet_h, cta_warps, depth, persistent, regcap, region, group;
 };
 
 // A planned kernel launch.

@@ -261,40 +261,36 @@ __device__ __forceinline__ RayBox grid_box(const VolDev &vol, const ViewDev &V)
     return B;
 }
 
-// Marches the ray of pixel (p, q) of one image through box B.  Direct
-// (PARTIAL false): stores the pixel value (Eq. 19, with the prefactor) and,
-// if cnt_img is set, its cell-sample count, or adds them to what is there
-// when `accumulate` is set (one thread owns each pixel, so the adds of
-// successive launches land in launch order).  PARTIAL: adds the ray's sum over
-// the box, without the prefactor, to out_img[pixel] if the ray sampled at
-// least one cell there (one region per slot and ray, so the add lands on
-// zero).  tab points at the march tables (shared memory when SMEM).
-//
-// NCH > 0 (vector renders, Sec. 2.1): the volume carries NCH more emissivity
-// channels sharing its velocity; each is summed with the same weights and
-// Doppler factors as j' (Eq. 19 per channel) into component c + 1 of the
-// pixel, at out_img + (c + 1) * width * height.
-//
-// TOUCH (memory analysis, not a render): instead of reading the two records
-// of a sample, set the bits of (snapshot, cell) in the bitmap `touch`, whose
-// bit m * cell_stride + cell stands for that record.
-struct ChanPtrs {
-    const float *chan;
-    long long comp_stride, cell_stride;
-    uint32_t *touch;
+// State of a ray during the march: per axis the next crossing, the current
+// cell's chord start (the latest face crossed) and its epoch coordinate.
+struct RayState {
+    AxisState ax[3];
+    float s_cur;       // s of the latest face crossed
+    long long u_cur;   // epoch coordinate there, Q31.32
+    bool alive;
+#ifdef GBD_CHECKED
+    int kc[3], kd[3];  // current cell in the volume's own frame, and its step per axis
+#endif
 };
 
-template <int STORE, int DEPTH, bool PAIRED, bool SMEM, bool PARTIAL = false, int NCH = 0, bool TOUCH = false>
-__device__ __forceinline__ void march_ray(const VolDev &vol, const ViewDev &V, const RayBox &B, int p, int q,
-                                          int width, int height, float *out_img, uint32_t *cnt_img, int *err_word,
-                                          const int32_t *__restrict__ tab, bool accumulate = false,
-                                          const ChanPtrs ch = ChanPtrs{nullptr, 0, 0, nullptr})
+// Ray set-up, once per ray, no float64: the anchor at the later of the box
+// entry and the window start [win_lo, win_hi] (a view's own window, or the
+// union of a group's), its cell and crossings, and the leading empty chords
+// stepped through, so that the march proper starts on the first cell whose
+// chord is positive.
+template <bool SMEM>
+__device__ __forceinline__ void setup_ray(RayState &R, const VolDev &vol, const ViewDev &V, const RayBox &B, int p,
+                                          int q, bool in_image, float win_lo, float win_hi,
+                                          const int32_t *__restrict__ tab)
 {
-    using Rec = Record<STORE>;
-    const bool in_image = (p < width) && (q < height);
-    bool alive = in_image;
-
-    // ---------------- ray setup, once per ray, no float64 ----------------
+    AxisState (&ax)[3] = R.ax;
+    bool &alive = R.alive;
+    float &s_cur = R.s_cur;
+    long long &u_cur = R.u_cur;
+#ifdef GBD_CHECKED
+    int (&kc)[3] = R.kc;
+#endif
+    alive = in_image;
     // Pixel position on the image plane in grid-index units (Q24.40, exact
     // integer arithmetic from the per-view constants), in the frame where
     // every axis is marched upwards.
@@ -318,8 +314,8 @@ __device__ __forceinline__ void march_ray(const VolDev &vol, const ViewDev &V, c
             alive = false;  // parallel to this axis and outside the box along it
         }
     }
-    const float s_a = fmaxf(s_in_e, V.win_lo);
-    if (!(fminf(s_out_e, V.win_hi) > s_a - 1e-3f * (1.f + fabsf(s_a)))) alive = false;
+    const float s_a = fmaxf(s_in_e, win_lo);
+    if (!(fminf(s_out_e, win_hi) > s_a - 1e-3f * (1.f + fabsf(s_a)))) alive = false;
     const float sa = alive ? s_a : 0.f;
 
     // Anchor: the point s_a of the ray, in exact fixed point; its cell (k,
@@ -327,12 +323,8 @@ __device__ __forceinline__ void march_ray(const VolDev &vol, const ViewDev &V, c
     // the face spacing along the ray (inv_a, Eq. 11), so that the crossing of
     // the plane nk cells above the cell's lower face is at nk inv_a - o inv_a.
     const long long u_a = V.u_obs - dd_mul_fix(sa, V.kk_hi, V.kk_lo, kTwo32);
-    AxisState ax[3];
-    float s_cur = -3.0e38f;  // the latest entry face of the anchor cell
-    long long u_cur = 0;
-#ifdef GBD_CHECKED
-    int kc[3];
-#endif
+    s_cur = -3.0e38f;  // the latest entry face of the anchor cell
+    u_cur = 0;
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
         const bool moving = V.inv_a[i] != 0.f;
@@ -373,6 +365,9 @@ __device__ __forceinline__ void march_ray(const VolDev &vol, const ViewDev &V, c
     const int kd0 = (V.flags & kFlagMirror0) ? -1 : 1;
     const int kd1 = (V.flags & (kFlagMirror0 << 1)) ? -1 : 1;
     const int kd2 = (V.flags & (kFlagMirror0 << 2)) ? -1 : 1;
+    R.kd[0] = kd0;
+    R.kd[1] = kd1;
+    R.kd[2] = kd2;
 #endif
 
     // Leading empty chords: when the anchor cell was clamped onto the grid, or
@@ -400,6 +395,51 @@ __device__ __forceinline__ void march_ray(const VolDev &vol, const ViewDev &V, c
             }
         }
     }
+}
+
+// Marches the ray of pixel (p, q) of one image through box B.  Direct
+// (PARTIAL false): stores the pixel value (Eq. 19, with the prefactor) and,
+// if cnt_img is set, its cell-sample count, or adds them to what is there
+// when `accumulate` is set (one thread owns each pixel, so the adds of
+// successive launches land in launch order).  PARTIAL: adds the ray's sum over
+// the box, without the prefactor, to out_img[pixel] if the ray sampled at
+// least one cell there (one region per slot and ray, so the add lands on
+// zero).  tab points at the march tables (shared memory when SMEM).
+//
+// NCH > 0 (vector renders, Sec. 2.1): the volume carries NCH more emissivity
+// channels sharing its velocity; each is summed with the same weights and
+// Doppler factors as j' (Eq. 19 per channel) into component c + 1 of the
+// pixel, at out_img + (c + 1) * width * height.
+//
+// TOUCH (memory analysis, not a render): instead of reading the two records
+// of a sample, set the bits of (snapshot, cell) in the bitmap `touch`, whose
+// bit m * cell_stride + cell stands for that record.
+struct ChanPtrs {
+    const float *chan;
+    long long comp_stride, cell_stride;
+    uint32_t *touch;
+};
+
+template <int STORE, int DEPTH, bool PAIRED, bool SMEM, bool PARTIAL = false, int NCH = 0, bool TOUCH = false>
+__device__ __forceinline__ void march_ray(const VolDev &vol, const ViewDev &V, const RayBox &B, int p, int q,
+                                          int width, int height, float *out_img, uint32_t *cnt_img, int *err_word,
+                                          const int32_t *__restrict__ tab, bool accumulate = false,
+                                          const ChanPtrs ch = ChanPtrs{nullptr, 0, 0, nullptr})
+{
+    using Rec = Record<STORE>;
+    const bool in_image = (p < width) && (q < height);
+    RayState R;
+    setup_ray<SMEM>(R, vol, V, B, p, q, in_image, V.win_lo, V.win_hi, tab);
+    AxisState (&ax)[3] = R.ax;
+    bool &alive = R.alive;
+    float &s_cur = R.s_cur;
+    long long &u_cur = R.u_cur;
+    const float ia0 = V.inv_a[0], ia1 = V.inv_a[1], ia2 = V.inv_a[2];
+    const long long du0 = V.du[0], du1 = V.du[1], du2 = V.du[2];
+#ifdef GBD_CHECKED
+    int (&kc)[3] = R.kc;
+    const int kd0 = R.kd[0], kd1 = R.kd[1], kd2 = R.kd[2];
+#endif
     const int Mm1 = vol.M - 1;
 
     BoostConsts bc;
@@ -578,6 +618,167 @@ __device__ __forceinline__ void march_ray(const VolDev &vol, const ViewDev &V, c
     }
 }
 
+// Time groups (batched renders).  Views that differ only in observer time
+// (and so in window and prefactor) share their rays; one lane marches its ray
+// once for up to kGroupMax such views.  The traversal covers the union of the
+// members' windows and carries the epoch coordinate of the reference member,
+// the one whose window ends last (largest u_obs); member g's coordinate
+// differs from it by the exact constant Delta_g = u_obs,g - u_obs,ref <= 0
+// (Q31.32), so at a chord midpoint it is um + Delta_g.  Per cell the
+// traversal is done once, and every member whose window some lane of the warp
+// reaches gathers, boosts and sums its own two snapshots into its own
+// compensated sum (Eq. 19 per view).  A member's pixel is summed over the same
+// cells, chords and midpoints as when its view is marched alone; the crossings
+// are measured from the group's anchor instead of the view's own, so the two
+// agree to float rounding, not bit for bit.  Member g's image is at
+// out + g * img_stride.
+template <int STORE, int DEPTH, bool PAIRED, int G>
+__device__ __forceinline__ void march_group(const VolDev &vol, const ViewDev &V, float win_lo, float win_hi,
+                                            const ViewDev *GV, const long long *dl, const int *dh, int gcnt,
+                                            const RayBox &B, int p, int q, int width, int height, float *out,
+                                            long long img_stride, uint32_t *cnt_img, int *err_word,
+                                            const int32_t *__restrict__ tab)
+{
+    using Rec = Record<STORE>;
+    const bool in_image = (p < width) && (q < height);
+    RayState R;
+    setup_ray<true>(R, vol, V, B, p, q, in_image, win_lo, win_hi, tab);
+    AxisState (&ax)[3] = R.ax;
+    bool &alive = R.alive;
+    float &s_cur = R.s_cur;
+    long long &u_cur = R.u_cur;
+    const float ia0 = V.inv_a[0], ia1 = V.inv_a[1], ia2 = V.inv_a[2];
+    const long long du0 = V.du[0], du1 = V.du[1], du2 = V.du[2];
+#ifdef GBD_CHECKED
+    int (&kc)[3] = R.kc;
+    const int kd0 = R.kd[0], kd1 = R.kd[1], kd2 = R.kd[2];
+#endif
+    const int Mm1 = vol.M - 1;
+
+    BoostConsts bc;
+    bc.shx = V.sh_hi[0]; bc.shy = V.sh_hi[1]; bc.shz = V.sh_hi[2];
+    bc.slx = V.sh_lo[0]; bc.sly = V.sh_lo[1]; bc.slz = V.sh_lo[2];
+    bc.expo = V.expo;
+    bc.beaming = (V.flags & GBD_BEAMING) != 0u;
+    const long long es = vol.epoch_stride;
+    const void *recs = vol.rec;
+
+    float acc[G], comp[G];
+    uint32_t count[G];
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+        acc[g] = comp[g] = 0.f;
+        count[g] = 0u;
+    }
+
+    while (__any_sync(kFull, alive)) {
+        long long um[DEPTH];  // reference epoch coordinate at the chord midpoint
+        float dsv[DEPTH];
+        int sm[DEPTH];        // layout offset of the cell
+        bool pos[DEPTH];      // a positive chord
+#ifdef GBD_CHECKED
+        int kcs[DEPTH][3];
+#endif
+        int mlo = INT_MAX, mhi = INT_MIN;  // the warp's range of reference snapshot indices
+#pragma unroll
+        for (int d = 0; d < DEPTH; ++d) {
+            um[d] = 0;
+            dsv[d] = 0.f;
+            sm[d] = 0;
+            pos[d] = false;
+            if (alive) {
+                const bool x0 = ax[0].sn <= ax[1].sn && ax[0].sn <= ax[2].sn;
+                const bool x1 = !x0 && ax[1].sn <= ax[2].sn;
+                const float s_exit = x0 ? ax[0].sn : (x1 ? ax[1].sn : ax[2].sn);
+                const long long u_exit = x0 ? ax[0].un : (x1 ? ax[1].un : ax[2].un);
+                const float ds = s_exit - s_cur;
+                um[d] = (u_cur + u_exit) >> 1;
+                pos[d] = ds > 0.f;
+                if (pos[d]) {
+                    const int mb = static_cast<int>(um[d] >> 32);
+                    mlo = min(mlo, mb);
+                    mhi = max(mhi, mb);
+                }
+                sm[d] = ax[0].o + ax[1].o + ax[2].o;
+                dsv[d] = ds;
+#ifdef GBD_CHECKED
+                kcs[d][0] = kc[0];
+                kcs[d][1] = kc[1];
+                kcs[d][2] = kc[2];
+#endif
+                step_exit<true>(ax, x0, x1, ia0, ia1, ia2, du0, du1, du2, tab);
+#ifdef GBD_CHECKED
+                kc[0] += x0 ? kd0 : 0;
+                kc[1] += x1 ? kd1 : 0;
+                kc[2] += (!x0 && !x1) ? kd2 : 0;
+#endif
+                s_cur = s_exit;
+                u_cur = u_exit;
+                alive = static_cast<int>(u_exit >> 32) >= -1 && (ax[0].o | ax[1].o | ax[2].o) >= 0;
+            }
+        }
+        mlo = __reduce_min_sync(kFull, mlo);
+        mhi = __reduce_max_sync(kFull, mhi);
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+            // Member g's snapshot index at a midpoint is mb + dh[g] or one
+            // more (dh = Delta_g rounded down to whole epochs): skip it when
+            // no lane of the warp can reach [-1, M - 1].
+            if (g >= gcnt || mlo > mhi || static_cast<long long>(mhi) + dh[g] < -2 ||
+                static_cast<long long>(mlo) + dh[g] > Mm1)
+                continue;
+            typename Rec::T rlo[DEPTH], rhi[DEPTH];
+            float wg[DEPTH];
+            bool take[DEPTH];
+#pragma unroll
+            for (int d = 0; d < DEPTH; ++d) {
+                const long long ug = um[d] + dl[g];
+                const int mb = static_cast<int>(ug >> 32);
+                const uint32_t frac = static_cast<uint32_t>(ug);
+                wg[d] = static_cast<float>(frac) * 2.3283064365386963e-10f;
+                const bool inside = pos[d] && static_cast<unsigned>(mb + 1) <= static_cast<unsigned>(Mm1 + 1);
+                bool has_lo = inside && mb >= 0;
+                bool has_hi = inside && (mb < Mm1) && (frac != 0u);
+#ifdef GBD_CHECKED
+                if ((has_lo && !check_cell(vol, err_word, kcs[d][0], kcs[d][1], kcs[d][2], mb)) ||
+                    (has_hi && !check_cell(vol, err_word, kcs[d][0], kcs[d][1], kcs[d][2], mb + 1)))
+                    has_lo = has_hi = false;
+#endif
+                take[d] = has_lo || has_hi;
+                rlo[d] = Rec::zero();
+                rhi[d] = Rec::zero();
+                if (PAIRED) {
+                    if (take[d]) Rec::load_pair(recs, static_cast<long long>(mb + 1) * es + 2LL * sm[d], rlo[d], rhi[d]);
+                } else {
+                    if (has_lo) rlo[d] = Rec::load(recs, static_cast<long long>(mb) * es + sm[d]);
+                    if (has_hi) rhi[d] = Rec::load(recs, static_cast<long long>(mb + 1) * es + sm[d]);
+                }
+            }
+#pragma unroll
+            for (int d = 0; d < DEPTH; ++d) {
+                const float vlo = Rec::boosted(rlo[d], bc);
+                const float vhi = Rec::boosted(rhi[d], bc);
+                const float v = fmaf(wg[d], vhi - vlo, vlo);       // Eq. 8
+                const float y = fmaf(v, dsv[d], -comp[g]);         // compensated sum
+                const float t = acc[g] + y;
+                comp[g] = take[d] ? (t - acc[g]) - y : comp[g];
+                acc[g] = take[d] ? t : acc[g];
+                count[g] += take[d] ? 1u : 0u;
+            }
+        }
+    }
+
+    if (in_image) {
+        const long long pix = static_cast<long long>(q) * width + p;
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+            if (g >= gcnt) break;
+            out[g * img_stride + pix] = GV[g].prefactor * acc[g];
+            if (cnt_img) cnt_img[g * img_stride + pix] = count[g];
+        }
+    }
+}
+
 // MINB = 1 leaves the register count to the compiler; MINB = 3 asks for
 // three 256-thread CTAs per SM (at most 80 registers per thread).
 //
@@ -626,6 +827,60 @@ __global__ void __launch_bounds__(256, MINB) march_kernel(const __grid_constant_
         const int q = ty * a.packet_h + lane / a.packet_w;
         march_ray<STORE, DEPTH, PAIRED, true>(a.vol, V, box, p, q, a.width, a.height, out, cnt, a.error_word, s_tab,
                                               a.accumulate != 0);
+        if (!a.persistent) break;
+    }
+}
+
+// Time groups: march_kernel's work split over groups of views instead of
+// single views (group g is views group_first[g] .. group_first[g + 1] - 1,
+// its CTAs cta_begin[g] .. cta_begin[g + 1] - 1, its tile counter queue[g]).
+// One cell per step (the members' gathers are the independent loads) and at
+// most 80 registers: with the compiler's budget (110 - 150) fewer warps fit
+// and the grouped march ran slower than the lone one.
+template <int STORE, int DEPTH, bool PAIRED, int G>
+__global__ void __launch_bounds__(256, 3) group_kernel(const __grid_constant__ MarchArgs a)
+{
+    extern __shared__ int32_t s_tab[];
+    const int ntab = march_table_entries(a.vol.n);
+    for (int i = threadIdx.x; i < ntab; i += blockDim.x) s_tab[i] = a.vol.mtab[i];
+    __syncthreads();
+
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int wpc = blockDim.x >> 5;
+    const int b = static_cast<int>(blockIdx.x);
+    int gi = 0, hi = a.n_groups - 1;  // last group whose first CTA is <= b
+    while (gi < hi) {
+        const int mid = (gi + hi + 1) >> 1;
+        if (a.cta_begin[mid] <= b) gi = mid;
+        else hi = mid - 1;
+    }
+    const int cb = b - a.cta_begin[gi];
+    const int first = a.group_first[gi];
+    const int gcnt = a.group_first[gi + 1] - first;
+    const ViewDev *GV = a.views + first;
+    const ViewDev &V = a.views[a.group_ref[gi]];
+    const float win_lo = a.group_win[gi][0], win_hi = a.group_win[gi][1];
+    const RayBox box = grid_box(a.vol, V);
+    const int tiles = a.tiles_x * a.tiles_y;
+    const long long stride = a.img_stride ? a.img_stride : static_cast<long long>(a.width) * a.height;
+    float *out = a.out + first * stride;
+    uint32_t *cnt = a.samples ? a.samples + first * stride : nullptr;
+    int tile = cb * wpc + warp;
+    for (;;) {
+        if (a.persistent) {
+            int it = 0;
+            if (lane == 0) it = atomicAdd(a.queue + gi, 1);
+            tile = __shfl_sync(kFull, it, 0);
+        }
+        if (tile >= tiles) break;
+        const int tx = tile % a.tiles_x;
+        const int ty = tile / a.tiles_x;
+        const int p = tx * a.packet_w + lane % a.packet_w;
+        const int q = ty * a.packet_h + lane / a.packet_w;
+        march_group<STORE, DEPTH, PAIRED, G>(a.vol, V, win_lo, win_hi, GV, a.view_delta + first, a.view_dhi + first,
+                                             gcnt, box, p, q, a.width, a.height, out, stride, cnt, a.error_word,
+                                             s_tab);
         if (!a.persistent) break;
     }
 }
@@ -866,6 +1121,25 @@ void *select_cap(int depth, int capped)
     return capped ? select_depth<STORE, 3, PAIRED>(depth) : select_depth<STORE, 1, PAIRED>(depth);
 }
 
+template <int STORE, bool PAIRED>
+void *select_group_size(int size)
+{
+    if (size == 4) return reinterpret_cast<void *>(&group_kernel<STORE, 1, PAIRED, 4>);
+    if (size == kGroupMax) return reinterpret_cast<void *>(&group_kernel<STORE, 1, PAIRED, kGroupMax>);
+    return nullptr;
+}
+
+// Time groups: a kernel for groups of up to 4 views and one for up to 8.
+void *select_group(int store, int paired, int size)
+{
+    if (store == GBD_STORE_F32)
+        return paired ? select_group_size<GBD_STORE_F32, true>(size) : select_group_size<GBD_STORE_F32, false>(size);
+    if (store == GBD_STORE_BF16_F16U)
+        return paired ? select_group_size<GBD_STORE_BF16_F16U, true>(size)
+                      : select_group_size<GBD_STORE_BF16_F16U, false>(size);
+    return nullptr;
+}
+
 void *select_kernel(int store, int depth, int capped, int paired)
 {
     if (store == GBD_STORE_F32)
@@ -1013,8 +1287,22 @@ cudaError_t launch_reduce(const ReduceArgs &a, cudaStream_t stream)
 
 cudaError_t plan_march(MarchArgs &a, const LaunchCfg &cfg, int num_sms, const double *work, KernelLaunch &L)
 {
-    void *k = select_kernel(a.vol.store, cfg.depth, cfg.regcap, a.vol.paired);
+    // n_groups > 0: time groups, one unit of CTAs per group; else one per view
+    const bool grouped = a.n_groups > 0;
+    void *k = grouped ? select_group(a.vol.store, a.vol.paired, a.group_size)
+                      : select_kernel(a.vol.store, cfg.depth, cfg.regcap, a.vol.paired);
     if (!k || a.n_views < 1 || a.n_views > kViewsPerLaunch) return cudaErrorInvalidValue;
+    if (grouped && (a.n_groups > a.n_views || a.group_first[0] != 0 || a.group_first[a.n_groups] != a.n_views))
+        return cudaErrorInvalidValue;
+    const int units = grouped ? a.n_groups : a.n_views;
+    double uwork[kViewsPerLaunch];
+    for (int u = 0; u < units; ++u) {
+        uwork[u] = 0.0;
+        const int v0 = grouped ? a.group_first[u] : u, v1 = grouped ? a.group_first[u + 1] : u + 1;
+        if (grouped && (v1 <= v0 || v1 - v0 > a.group_size || a.group_ref[u] < v0 || a.group_ref[u] >= v1))
+            return cudaErrorInvalidValue;
+        for (int v = v0; v < v1; ++v) uwork[u] += work ? std::max(work[v], 0.0) : 1.0;
+    }
     const int threads = 32 * cfg.cta_warps;
     const int smem = static_cast<int>(sizeof(int32_t)) * march_table_entries(a.vol.n);
     if (smem > 48 * 1024) {
@@ -1033,21 +1321,21 @@ cudaError_t plan_march(MarchArgs &a, const LaunchCfg &cfg, int num_sms, const do
         if (per_sm < 1) per_sm = 1;
         const long long resident = static_cast<long long>(per_sm) * num_sms;
         double sum = 0.0;
-        for (int v = 0; v < a.n_views; ++v) sum += work ? std::max(work[v], 0.0) : 1.0;
-        for (int v = 0; v < a.n_views; ++v) {
-            const double share = sum > 0.0 ? (work ? std::max(work[v], 0.0) : 1.0) / sum : 1.0 / a.n_views;
+        for (int u = 0; u < units; ++u) sum += uwork[u];
+        for (int u = 0; u < units; ++u) {
+            const double share = sum > 0.0 ? uwork[u] / sum : 1.0 / units;
             const long long c = std::min(needed, std::max(1LL, static_cast<long long>(share * resident + 0.5)));
-            a.cta_begin[v] = static_cast<int>(total);
+            a.cta_begin[u] = static_cast<int>(total);
             total += c;
         }
     } else {
-        for (int v = 0; v < a.n_views; ++v) {
-            a.cta_begin[v] = static_cast<int>(total);
+        for (int u = 0; u < units; ++u) {
+            a.cta_begin[u] = static_cast<int>(total);
             total += needed;
         }
     }
     if (total < 1 || total > 0x7fffffffLL) return cudaErrorInvalidValue;
-    a.cta_begin[a.n_views] = static_cast<int>(total);
+    a.cta_begin[units] = static_cast<int>(total);
     L.func = k;
     L.grid = dim3(static_cast<unsigned>(total));
     L.block = dim3(threads);

@@ -86,6 +86,7 @@ extern "C" int gbd_render_batch_noalloc(gbd_ctx *ctx, gbd_volume vid, const gbd_
     const int chunks = march_chunks(n);
     for (int c = 0; c < chunks && e == cudaSuccess; ++c) {
         fill_args(g_args, *vol, g_host_views, n, c, *spec, spec->out, spec->samples, queue, cfg, ctx->err_word);
+        group_views(g_args, cfg.group);
         for (int v = 0; v < g_args.n_views; ++v)
             g_work[v] = view_work(*vol, g_args.views[v], spec->width, spec->height);
         e = launch_march(g_args, cfg, ctx->num_sms, g_work, st);

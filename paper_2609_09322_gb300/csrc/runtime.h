@@ -44,7 +44,7 @@ struct TuneKey {
 };
 
 struct TuneEntry {
-    LaunchCfg cfg{8, 4, 8, 2, 1, 0, 0};
+    LaunchCfg cfg{8, 4, 8, 2, 1, 0, 0, kGroupDefault};
     int brick = 8, super_brick = 4;
     float ms = 0.f;
 };
@@ -115,6 +115,8 @@ cudaError_t enqueue_regions(Ctx &ctx, const Volume &vol, const std::vector<ViewD
 std::vector<double> view_works(const Volume &vol, const std::vector<ViewDev> &hv, int width, int height);
 void fill_args(MarchArgs &a, const Volume &vol, const ViewDev *hv, int n, int c, const gbd_image_spec &s,
                float *out, uint32_t *samples, int *queue, const LaunchCfg &cfg, int *err_word);
+// Time groups of a filled launch (batched renders; see MarchArgs).
+void group_views(MarchArgs &a, int gmax);
 bool build_layout(const int n[3], int B, int S, std::vector<int32_t> &tab, long long &epoch_stride, int morton_cells);
 void destroy_graph_cache(GraphCache *g);
 

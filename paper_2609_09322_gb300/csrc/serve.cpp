@@ -70,7 +70,7 @@ struct Server {
     Ctx *ctx = nullptr;
     int device = 0;
     gbd_serve_config cfg{};
-    LaunchCfg launch{8, 4, 8, 1, 1, 0, 0};
+    LaunchCfg launch{8, 4, 8, 1, 1, 0, 0, 1};
     uint64_t request_budget = 0;
     std::mutex mu;
     std::condition_variable cv;       // wakes the scheduler

@@ -56,9 +56,9 @@ void append_cache_file(const TuneKey &k, const TuneEntry &e)
     std::lock_guard<std::mutex> lock(g_file_mu);
     FILE *f = std::fopen(path, "a");
     if (!f) return;
-    std::fprintf(f, "%s -> %d %d %d %d %d %d %d %d %d %.6f\n", key_text(k).c_str(), e.cfg.packet_w, e.cfg.packet_h,
-                 e.cfg.cta_warps, e.cfg.depth, e.cfg.persistent, e.cfg.regcap, e.cfg.region, e.brick, e.super_brick,
-                 e.ms);
+    std::fprintf(f, "%s -> %d %d %d %d %d %d %d %d %d %d %.6f\n", key_text(k).c_str(), e.cfg.packet_w,
+                 e.cfg.packet_h, e.cfg.cta_warps, e.cfg.depth, e.cfg.persistent, e.cfg.regcap, e.cfg.region,
+                 e.cfg.group, e.brick, e.super_brick, e.ms);
     std::fclose(f);
 }
 
@@ -92,6 +92,7 @@ int time_config(Ctx &ctx, const Volume &vol, const std::vector<ViewDev> &hv, con
         for (int c = 0; c < chunks && e == cudaSuccess && slots == 0; ++c) {
             fill_args(*args, vol, hv.data(), n, c, spec, spec.out, nullptr, reinterpret_cast<int *>(scratch), cfg,
                       ctx.err_word);
+            group_views(*args, cfg.group);
             e = launch_march(*args, cfg, ctx.num_sms, work.data() + static_cast<size_t>(c) * kViewsPerLaunch, st);
         }
         if (e == cudaSuccess) e = cudaEventRecord(b, st);
@@ -235,10 +236,10 @@ void load_tune_file(Ctx &ctx)
         TuneKey k;
         std::memset(&k, 0, sizeof(k));
         TuneEntry e;
-        if (std::sscanf(line, "%d %d %d %d %d %d %d %d %d -> %d %d %d %d %d %d %d %d %d %f", &k.n[0], &k.n[1],
+        if (std::sscanf(line, "%d %d %d %d %d %d %d %d %d -> %d %d %d %d %d %d %d %d %d %d %f", &k.n[0], &k.n[1],
                         &k.n[2], &k.M, &k.store, &k.width, &k.height, &k.n_views, &k.lookback, &e.cfg.packet_w,
                         &e.cfg.packet_h, &e.cfg.cta_warps, &e.cfg.depth, &e.cfg.persistent, &e.cfg.regcap,
-                        &e.cfg.region, &e.brick, &e.super_brick, &e.ms) == 19 &&
+                        &e.cfg.region, &e.cfg.group, &e.brick, &e.super_brick, &e.ms) == 20 &&
             check_launch(e.cfg) == GBD_OK)
             ctx.tuned[k] = e;  // later lines win
     }
@@ -290,11 +291,12 @@ int gbd_tune(gbd_ctx *ctx, gbd_volume vid, const gbd_view *views, int32_t n, con
     auto report = [&](const LaunchCfg &c, float ms, int B, int S) {
         if (verbose)
             std::fprintf(stderr,
-                         "gbd_tune: packet %2dx%-2d warps %d depth %d persistent %d regcap %d region %d layout %d/%d: "
-                         "%.4f ms\n",
-                         c.packet_w, c.packet_h, c.cta_warps, c.depth, c.persistent, c.regcap, c.region, B, S, ms);
+                         "gbd_tune: packet %2dx%-2d warps %d depth %d persistent %d regcap %d region %d group %d "
+                         "layout %d/%d: %.4f ms\n",
+                         c.packet_w, c.packet_h, c.cta_warps, c.depth, c.persistent, c.regcap, c.region, c.group, B, S,
+                         ms);
     };
-    LaunchCfg best{8, 4, 8, 2, 1, 0, 0};
+    LaunchCfg best{8, 4, 8, 2, 1, 0, 0, kGroupDefault};
     float best_ms = 0.f;
     int tried = 0;
     if ((rc = time_config(*ctx, *vol, hv, *spec, best, st, 3, best_ms))) return rc;
@@ -308,7 +310,7 @@ int gbd_tune(gbd_ctx *ctx, gbd_volume vid, const gbd_view *views, int32_t n, con
             for (const auto &pk : packets)
                 for (int w : warps)
                     for (int d : depths) {
-                        LaunchCfg c{pk[0], pk[1], w, d, 1, cap, 0};
+                        LaunchCfg c{pk[0], pk[1], w, d, 1, cap, 0, kGroupDefault};
                         float ms = 0.f;
                         if ((rc = time_config(*ctx, *vol, hv, *spec, c, st, 3, ms))) return rc;
                         report(c, ms, vol->brick, vol->super_brick);
@@ -318,7 +320,7 @@ int gbd_tune(gbd_ctx *ctx, gbd_volume vid, const gbd_view *views, int32_t n, con
                             best = c;
                         }
                     }
-        LaunchCfg flat{8, 4, 8, 2, 0, 0, 0};
+        LaunchCfg flat{8, 4, 8, 2, 0, 0, 0, kGroupDefault};
         float ms = 0.f;
         if ((rc = time_config(*ctx, *vol, hv, *spec, flat, st, 3, ms))) return rc;
         report(flat, ms, vol->brick, vol->super_brick);
@@ -338,7 +340,7 @@ int gbd_tune(gbd_ctx *ctx, gbd_volume vid, const gbd_view *views, int32_t n, con
                     for (const auto &pk : rpackets)
                         for (int w : rwarps)
                             for (int d = 1; d <= 2; ++d) {
-                                LaunchCfg c{pk[0], pk[1], w, d, 0, cap, reg};
+                                LaunchCfg c{pk[0], pk[1], w, d, 0, cap, reg, kGroupDefault};
                                 if (region_slots(*vol, c, *spec, nreg) == 0) continue;
                                 float rms = 0.f;
                                 if ((rc = time_config(*ctx, *vol, hv, *spec, c, st, 3, rms))) return rc;
@@ -349,6 +351,23 @@ int gbd_tune(gbd_ctx *ctx, gbd_volume vid, const gbd_view *views, int32_t n, con
                                     best = c;
                                 }
                             }
+        }
+        // time groups: up to kGroupDefault views per ray is the default;
+        // none (1), smaller or larger groups are tried against it
+        if (best.region == 0) {
+            const LaunchCfg base = best;
+            for (int gsz : {1, 2, kGroupMax}) {
+                LaunchCfg c = base;
+                c.group = gsz;
+                float gms = 0.f;
+                if ((rc = time_config(*ctx, *vol, hv, *spec, c, st, 3, gms))) return rc;
+                report(c, gms, vol->brick, vol->super_brick);
+                ++tried;
+                if (gms < best_ms) {
+                    best_ms = gms;
+                    best = c;
+                }
+            }
         }
     }
     if (what & GBD_TUNE_LAYOUT) {
@@ -396,6 +415,7 @@ int gbd_tune(gbd_ctx *ctx, gbd_volume vid, const gbd_view *views, int32_t n, con
     out->launch.persistent = best.persistent;
     out->launch.regcap = best.regcap;
     out->launch.region = best.region;
+    out->launch.group = best.group;
     out->brick = vol->brick;
     out->super_brick = vol->super_brick;
     out->paired = vol->paired;

@@ -63,7 +63,7 @@ class ImageSpec(ctypes.Structure):
 class Launch(ctypes.Structure):
     _fields_ = [("packet_w", ctypes.c_int32), ("packet_h", ctypes.c_int32), ("cta_warps", ctypes.c_int32),
                 ("depth", ctypes.c_int32), ("persistent", ctypes.c_int32), ("regcap", ctypes.c_int32),
-                ("region", ctypes.c_int32)]
+                ("region", ctypes.c_int32), ("group", ctypes.c_int32)]
 
 
 class TuneResult(ctypes.Structure):
@@ -205,6 +205,7 @@ def _launch(launch) -> ctypes.POINTER(Launch) | None:
     lw.persistent = int(launch.get("persistent", 1))
     lw.regcap = int(launch.get("regcap", 0))
     lw.region = int(launch.get("region", 0))
+    lw.group = int(launch.get("group", 0))
     return ctypes.pointer(lw)
 
 
@@ -506,7 +507,7 @@ class Context:
                                            _stream_handle(stream), ctypes.byref(res)))
         lw = res.launch
         return dict(packet=(lw.packet_w, lw.packet_h), cta_warps=lw.cta_warps, depth=lw.depth,
-                    persistent=lw.persistent, regcap=lw.regcap, region=lw.region, brick=res.brick,
+                    persistent=lw.persistent, regcap=lw.regcap, region=lw.region, group=lw.group, brick=res.brick,
                     super_brick=res.super_brick,
                     paired=res.paired, morton_cells=res.morton_cells, ms=res.ms, candidates=res.candidates)
 
