@@ -253,7 +253,10 @@ size_t volume_bytes(int store, long long cells_per_epoch, int M, int paired, lon
 {
     const size_t rec = store == GBD_STORE_F32 ? 16 : 8;
     *stride = paired ? 2 * cells_per_epoch : cells_per_epoch;
-    return rec * static_cast<size_t>(*stride) * static_cast<size_t>(paired ? M + 1 : M);
+    // paired: M + 1 blocks and one zero record pair after them, which a
+    // sample that reads no snapshot loads instead of skipping its load
+    return paired ? rec * (static_cast<size_t>(*stride) * static_cast<size_t>(M + 1) + 2)
+                  : rec * static_cast<size_t>(*stride) * static_cast<size_t>(M);
 }
 
 VolDev vol_dev(const Volume &v)

@@ -24,7 +24,8 @@ struct VolDev {
     const void *rec;          // record array (16-byte or 8-byte records)
     const int32_t *axis_off;  // n[0] + n[1] + n[2] entries
     const int32_t *mtab;      // march tables, march_table_entries(n) entries (see below)
-    long long epoch_stride;   // records per block (padded)
+    long long epoch_stride;   // records per block (padded); paired: a zero record pair
+                              // follows the M + 1 blocks, at record (M + 1) * epoch_stride
     int n[3];
     int M;
     int store;                // GBD_STORE_*

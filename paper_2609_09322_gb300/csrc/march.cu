@@ -129,9 +129,13 @@ struct Record<GBD_STORE_BF16_F16U> {
     static __device__ __forceinline__ float boost(const T r, const BoostConsts &c)
     {
         if (!c.beaming) return 1.0f;
-        const float ux = __half2float(__ushort_as_half(static_cast<unsigned short>(r.x >> 16)));
-        const float uy = __half2float(__ushort_as_half(static_cast<unsigned short>(r.y & 0xffffu)));
-        const float uz = __half2float(__ushort_as_half(static_cast<unsigned short>(r.y >> 16)));
+        // u_x is the high half of r.x, (u_y, u_z) the two halves of r.y
+        __half2 hx, hyz;
+        memcpy(&hx, &r.x, sizeof(hx));
+        memcpy(&hyz, &r.y, sizeof(hyz));
+        const float ux = __high2float(hx);
+        const float2 uyz = __half22float2(hyz);
+        const float uy = uyz.x, uz = uyz.y;
         const float us = fmaf(ux, c.shx, fmaf(uy, c.shy, uz * c.shz));
         const float uu = fmaf(ux, ux, fmaf(uy, uy, uz * uz));
         const float gp = sqrt_approx(1.0f + uu) + fabsf(us);
@@ -450,6 +454,11 @@ __device__ __forceinline__ void march_ray(const VolDev &vol, const ViewDev &V, c
 
     const long long es = vol.epoch_stride;
     const void *recs = vol.rec;
+    // Paired float32 records: a sample that reads no snapshot loads the zero
+    // record pair after the last block instead of skipping its loads (faster
+    // for the 32-byte pairs; for 16-byte pairs it costs registers and time).
+    constexpr bool kZeroPair = PAIRED && NCH == 0 && !TOUCH && STORE == GBD_STORE_F32;
+    const long long zero_off = static_cast<long long>(vol.M + 1) * es;
 
     float acc = 0.f, comp = 0.f;
     uint32_t count = 0;
@@ -470,7 +479,7 @@ __device__ __forceinline__ void march_ray(const VolDev &vol, const ViewDev &V, c
         for (int d = 0; d < DEPTH; ++d) {
             has_lo[d] = false;
             has_hi[d] = false;
-            off[d] = 0;
+            off[d] = kZeroPair ? zero_off : 0;
             coff[d] = 0;
             wgt[d] = 0.f;
             dsv[d] = 0.f;
@@ -501,8 +510,9 @@ __device__ __forceinline__ void march_ray(const VolDev &vol, const ViewDev &V, c
                     const int sum = ax[0].o + ax[1].o + ax[2].o;
                     // unpaired: snapshot m at block m; paired: snapshots mb and
                     // mb + 1 side by side in block mb + 1
-                    off[d] = PAIRED ? static_cast<long long>(mb + 1) * es + 2LL * sum
-                                    : static_cast<long long>(mb) * es + sum;
+                    if (!kZeroPair || has_lo[d] || has_hi[d])
+                        off[d] = PAIRED ? static_cast<long long>(mb + 1) * es + 2LL * sum
+                                        : static_cast<long long>(mb) * es + sum;
                     if constexpr (NCH > 0 || TOUCH) coff[d] = static_cast<long long>(mb) * ch.cell_stride + sum;
                     wgt[d] = w;
                     dsv[d] = ds;
@@ -532,6 +542,8 @@ __device__ __forceinline__ void march_ray(const VolDev &vol, const ViewDev &V, c
                     const long long i = coff[d] + ch.cell_stride;
                     atomicOr(ch.touch + (i >> 5), 1u << (i & 31));
                 }
+            } else if (kZeroPair) {
+                Rec::load_pair(recs, off[d], rlo[d], rhi[d]);  // the zero pair when it reads no snapshot
             } else if (PAIRED) {
                 rlo[d] = Rec::zero();
                 rhi[d] = Rec::zero();
