@@ -329,7 +329,14 @@ def run_gpu(args, rank: int, world: int):
     launches = args.steps * (n_views if args.per_image else ctx.last_launch_count())
 
     # end to end through the public API with host buffers
-    if args.form == "batch":
+    if args.form == "batch" and args.per_image:
+        # one call per view, each image copied back into its slice of pinned memory
+        host = torch.empty((n_views, views[0].height, views[0].width), dtype=torch.float32, pin_memory=True)
+
+        def e2e_step():
+            for k, v in enumerate(views):
+                ctx.render_batch_host(vol, [v], host[k], launch=launch, stream=stream)
+    elif args.form == "batch":
         host = torch.empty((n_views, views[0].height, views[0].width), dtype=torch.float32, pin_memory=True)
 
         def e2e_step():
@@ -396,7 +403,8 @@ def run_gpu(args, rank: int, world: int):
                      "kernel_ms_median": round(kernel_ms, 4)},
         "e2e": {"value": round(world * samples_per_step / e2e_s / 1e9, 4), "unit": UNIT,
                 "h2d_bytes_per_step": view_bytes, "d2h_bytes_per_step": img_bytes,
-                "note": "render_batch with host output: per-view constants H2D in the launch parameters, "
+                "note": ("one render call per view" if args.per_image else "render_batch")
+                        + " with host output: per-view constants H2D in the launch parameters, "
                         "images D2H into pinned memory, volume resident"},
         "gpu_launches": launches,
         **({"form": form_note} if form_note else {}),
