@@ -22,6 +22,10 @@
 // Cells are gathered DEPTH at a time: the traversal runs ahead, all loads of
 // the group are issued, then the group is evaluated, so each lane keeps up to
 // 2 * DEPTH independent loads in flight.
+//
+// Time groups (batched renders of one direction at several observer times):
+// one traversal per ray serves up to 4 or 8 views, each with its own sums
+// (march_group, group_kernel).
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
