@@ -417,6 +417,8 @@ def run_gpu(args, rank: int, world: int):
         "load_s": round(t_load, 3),
     }
     ctx.close()
+    # the last step's images, for the oracle comparison of the CPU-baseline leg
+    wl["gpu_images"] = (vout[:, 0] if args.form == "vector" else out).cpu().numpy()
     return result, clk.summary(), wl
 
 
@@ -536,9 +538,11 @@ def run_serving(args, rank: int, world: int):
 
 
 # ------------------------------------------------------------------ CPU oracle
-def oracle_sample(wl, seconds: float, seed: int = 0):
+def oracle_sample(wl, seconds: float, seed: int = 0, errors: list | None = None):
     """Times the oracle on a random sample of the workload's pixels until
-    about ``seconds`` of work; returns (cell-samples/s, pixels, threads)."""
+    about ``seconds`` of work; returns (cell-samples/s, pixels, threads).
+    With ``errors`` (and the GPU's images in wl), appends per batch the
+    oracle's values with the GPU's values of the same pixels."""
     import oracle
     rng = np.random.default_rng(seed)
     views = wl["views"]
@@ -546,17 +550,38 @@ def oracle_sample(wl, seconds: float, seed: int = 0):
     done_samples, done_pix, elapsed = 0, 0, 0.0
     batch = 256
     while elapsed < seconds:
-        v = views[int(rng.integers(len(views)))]
+        vi = int(rng.integers(len(views)))
+        v = views[vi]
         pix = np.stack([rng.integers(0, v.width, batch), rng.integers(0, v.height, batch)], axis=1)
         t0 = time.perf_counter()
-        _, cnt = oracle.render_pixels(wl["grid"], wl["j"], wl["beta"], v, pix, counts=True)
+        val, cnt = oracle.render_pixels(wl["grid"], wl["j"], wl["beta"], v, pix, counts=True)
         dt = time.perf_counter() - t0
         elapsed += dt
         done_samples += int(cnt.sum())
         done_pix += batch
+        if errors is not None and "gpu_images" in wl:
+            errors.append((val, wl["gpu_images"][vi][pix[:, 1], pix[:, 0]].astype(np.float64)))
         if dt < 0.5 * seconds / 4 and batch < 65536:
             batch *= 2
     return done_samples / elapsed / 1e9, done_pix, threads, elapsed
+
+
+def oracle_error(errors, store: str):
+    """The GPU's error on the oracle's sampled pixels, per pixel relative to
+    |I_ref| + 1e-3 max(I_ref) (the parity tests' floor).  For float32 storage
+    the oracle reads the same float32 fields as the GPU (kernel arithmetic);
+    for BF16/FP16 storage it reads the float32 fields the records were made
+    from (storage and arithmetic together)."""
+    ref = np.concatenate([e[0] for e in errors])
+    gpu = np.concatenate([e[1] for e in errors])
+    peak = float(np.abs(ref).max()) if ref.size else 0.0
+    rel = np.abs(gpu - ref) / (np.abs(ref) + 1e-3 * peak + 1e-300)
+    tol = 1e-5 if store == "f32" else 1e-2
+    return {"pixels": int(ref.size), "max_rel": float(f"{rel.max():.3g}"), "p99_rel": float(f"{np.quantile(rel, 0.99):.3g}"),
+            "within_tolerance": round(float((rel <= tol).mean()), 6), "tolerance": tol,
+            "flux_rel": float(f"{abs(gpu.sum() - ref.sum()) / max(abs(ref.sum()), 1e-300):.3g}"),
+            "reference": "FP64 oracle on the stored float32 fields" if store == "f32"
+                         else "FP64 oracle on the float32 fields the BF16/FP16 records were made from"}
 
 
 def run_reference(args, rank: int):
@@ -639,9 +664,12 @@ def main():
     result, clocks, wl = run_gpu(args, rank, world)
     result["clocks"] = clocks
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        rate, pix, threads, el = oracle_sample(wl, args.cpu_seconds)
+        errors = []
+        rate, pix, threads, el = oracle_sample(wl, args.cpu_seconds, errors=errors)
         result["cpu_baseline"] = {"value": round(rate, 6), "unit": UNIT, "cores": threads, "kind": "oracle",
                                   "sample": f"{pix} random pixels of the workload's views, {el:.1f} s"}
+        if errors:
+            result["oracle_error"] = oracle_error(errors, wl["store"])
     if rank == 0:
         print(json.dumps(result), flush=True)
     if world > 1:
