@@ -10,6 +10,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdarg>
+#include <cstdlib>
 #include <cstdio>
 #include <cstring>
 #include <map>
@@ -395,19 +396,24 @@ static bool same_rays(const ViewDev &x, const ViewDev &y)
            x.flags == y.flags;
 }
 
-// Time groups: each run of consecutive views with the same rays becomes
-// ceil(run / gmax) groups of near-equal size.  n_groups stays 0 (every view
-// marched on its own) when gmax < 2 or no run holds two views.
+// Time groups: each run of consecutive views with the same rays, whose
+// neighbours' windows overlap (epoch coordinates at the image plane at most
+// M + 1 snapshots apart, else the shared march would cross the gap between
+// them), becomes ceil(run / gmax) groups of near-equal size.  n_groups stays 0
+// (every view marched on its own) when gmax < 2 or no run holds two views.
 void group_views(MarchArgs &a, int gmax)
 {
     a.n_groups = 0;
     gmax = std::min(gmax, kGroupMax);
     if (gmax < 2) return;
+    const long long reach = static_cast<long long>(a.vol.M + 1) << 32;  // Q31.32
     int ng = 0;
     bool shared = false;
     for (int v = 0; v < a.n_views;) {
         int e = v + 1;
-        while (e < a.n_views && same_rays(a.views[v], a.views[e])) ++e;
+        while (e < a.n_views && same_rays(a.views[v], a.views[e]) &&
+               std::llabs(a.views[e].u_obs - a.views[e - 1].u_obs) <= reach)
+            ++e;
         const int len = e - v, parts = (len + gmax - 1) / gmax;
         for (int k = 0; k < parts; ++k) a.group_first[ng++] = v + len * k / parts;
         shared = shared || len > 1;
