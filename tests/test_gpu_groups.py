@@ -192,3 +192,23 @@ def test_time_series_at_bench_shape_sampled(ctx):
         sub = oracle.render_pixels(grid, j, beta, views[k], px)
         assert_parity(img[k][px[:, 1], px[:, 0]], sub, what=f"time-delay view {k} sampled")
     ctx.unload(vol)
+
+
+def test_groups_with_host_output_and_many_launches(ctx):
+    """Grouped batches to host memory equal the device images; a time series
+    longer than one launch (130 views: 128 + 2, a run cut at the launch
+    boundary) still matches the oracle view by view."""
+    grid, j, beta = random_grid(61, n=(10, 12, 9), M=5)
+    vol = ctx.load_snapshots(grid, j, beta, paired=True)
+    base = gen.view_from_angles(grid, 28.0, 64.0, size=10, fov=1.9 * float(np.max(grid.extent)), c=0.8)
+    views = time_series(base, np.linspace(-2.0, 11.0, 130))
+    dev, cnt = batch(ctx, vol, views)
+    host = torch.empty((130, 10, 10), dtype=torch.float32, pin_memory=True)
+    ctx.render_batch_host(vol, views, host)
+    torch.cuda.synchronize()
+    assert np.array_equal(host.numpy(), dev)
+    for k in (0, 1, 63, 126, 127, 128, 129):
+        ref, rcnt = oracle.render(grid, j, beta, views[k], counts=True)
+        assert_parity(dev[k], ref, what=f"long series view {k}")
+        assert np.abs(cnt[k] - rcnt).max() <= 1
+    ctx.unload(vol)
