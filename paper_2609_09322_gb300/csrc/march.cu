@@ -845,12 +845,13 @@ __device__ __forceinline__ void march_group(const VolDev &vol, const ViewDev &V,
 // three 256-thread CTAs per SM (at most 80 registers per thread).
 //
 // Each CTA works on one view, one packet per warp: its tile directly, or,
-// persistent, tiles pulled from the view's counter until none are left.  The
+// persistent, tiles pulled from the view's counter until none are left (with
+// STEAL, then from the other views' counters in turn).  The
 // CTAs of view v are cta_begin[v] .. cta_begin[v + 1] - 1 (persistent grids
 // give each view a share of the GPU in proportion to its estimated work); a
 // binary search over these parameter-space bounds keeps the view index
 // uniform across the CTA.
-template <int STORE, int DEPTH, int MINB, bool PAIRED>
+template <int STORE, int DEPTH, int MINB, bool PAIRED, bool STEAL>
 __global__ void __launch_bounds__(256, MINB) march_kernel(const __grid_constant__ MarchArgs a)
 {
     extern __shared__ int32_t s_tab[];
@@ -862,34 +863,65 @@ __global__ void __launch_bounds__(256, MINB) march_kernel(const __grid_constant_
     const int warp = threadIdx.x >> 5;
     const int wpc = blockDim.x >> 5;
     const int b = static_cast<int>(blockIdx.x);
-    int vi = 0, hi = a.n_views - 1;  // last view whose first CTA is <= b
-    while (vi < hi) {
-        const int mid = (vi + hi + 1) >> 1;
-        if (a.cta_begin[mid] <= b) vi = mid;
+    int home = 0, hi = a.n_views - 1;  // last view whose first CTA is <= b
+    while (home < hi) {
+        const int mid = (home + hi + 1) >> 1;
+        if (a.cta_begin[mid] <= b) home = mid;
         else hi = mid - 1;
     }
-    const int cb = b - a.cta_begin[vi];
-    const ViewDev &V = a.views[vi];
-    const RayBox box = grid_box(a.vol, V);
+    const int cb = b - a.cta_begin[home];
     const int tiles = a.tiles_x * a.tiles_y;
-    const long long img = static_cast<long long>(vi) * (a.img_stride ? a.img_stride : static_cast<long long>(a.width) * a.height);
-    float *out = a.out + img;
-    uint32_t *cnt = a.samples ? a.samples + img : nullptr;
-    int tile = cb * wpc + warp;
-    for (;;) {
-        if (a.persistent) {
-            int it = 0;
-            if (lane == 0) it = atomicAdd(a.queue + vi, 1);
-            tile = __shfl_sync(kFull, it, 0);
+    const long long stride = a.img_stride ? a.img_stride : static_cast<long long>(a.width) * a.height;
+    if constexpr (STEAL) {
+        // Persistent warps take their home view's tiles first, then, once
+        // its counter is spent, the other views' tiles in turn, so that no SM
+        // idles while any view of the launch has tiles left.  The view index
+        // depends on the CTA and the round only, and the exit test is a warp
+        // vote, so the view's constants stay warp-uniform.
+        const int rounds = a.persistent ? a.n_views : 1;
+        for (int r = 0; r < rounds; ++r) {
+            const int vi = home + r < a.n_views ? home + r : home + r - a.n_views;
+            const ViewDev &V = a.views[vi];
+            const RayBox box = grid_box(a.vol, V);
+            float *out = a.out + vi * stride;
+            uint32_t *cnt = a.samples ? a.samples + vi * stride : nullptr;
+            int tile = cb * wpc + warp;
+            for (;;) {
+                if (a.persistent) {
+                    int it = 0;
+                    if (lane == 0) it = atomicAdd(a.queue + vi, 1);
+                    tile = __shfl_sync(kFull, it, 0);
+                }
+                if (__any_sync(kFull, tile >= tiles)) break;
+                const int tx = tile % a.tiles_x;
+                const int ty = tile / a.tiles_x;
+                const int p = tx * a.packet_w + lane % a.packet_w;
+                const int q = ty * a.packet_h + lane / a.packet_w;
+                march_ray<STORE, DEPTH, PAIRED, true>(a.vol, V, box, p, q, a.width, a.height, out, cnt,
+                                                      a.error_word, s_tab, a.accumulate != 0);
+                if (!a.persistent) break;
+            }
         }
-        if (tile >= tiles) break;
-        const int tx = tile % a.tiles_x;
-        const int ty = tile / a.tiles_x;
-        const int p = tx * a.packet_w + lane % a.packet_w;
-        const int q = ty * a.packet_h + lane / a.packet_w;
-        march_ray<STORE, DEPTH, PAIRED, true>(a.vol, V, box, p, q, a.width, a.height, out, cnt, a.error_word, s_tab,
-                                              a.accumulate != 0);
-        if (!a.persistent) break;
+    } else {
+        // one view (or one packet per warp): the home view's tiles only
+        const ViewDev &V = a.views[home];
+        const RayBox box = grid_box(a.vol, V);
+        float *out = a.out + home * stride;
+        uint32_t *cnt = a.samples ? a.samples + home * stride : nullptr;
+        int tile = cb * wpc + warp;
+        for (;;) {
+            if (a.persistent) {
+                int it = 0;
+                if (lane == 0) it = atomicAdd(a.queue + home, 1);
+                tile = __shfl_sync(kFull, it, 0);
+            }
+            if (tile >= tiles) break;
+            const int p = (tile % a.tiles_x) * a.packet_w + lane % a.packet_w;
+            const int q = (tile / a.tiles_x) * a.packet_h + lane / a.packet_w;
+            march_ray<STORE, DEPTH, PAIRED, true>(a.vol, V, box, p, q, a.width, a.height, out, cnt, a.error_word,
+                                                  s_tab, a.accumulate != 0);
+            if (!a.persistent) break;
+        }
     }
 }
 
@@ -911,39 +943,44 @@ __global__ void __launch_bounds__(256, 3) group_kernel(const __grid_constant__ M
     const int warp = threadIdx.x >> 5;
     const int wpc = blockDim.x >> 5;
     const int b = static_cast<int>(blockIdx.x);
-    int gi = 0, hi = a.n_groups - 1;  // last group whose first CTA is <= b
-    while (gi < hi) {
-        const int mid = (gi + hi + 1) >> 1;
-        if (a.cta_begin[mid] <= b) gi = mid;
+    int home = 0, hi = a.n_groups - 1;  // last group whose first CTA is <= b
+    while (home < hi) {
+        const int mid = (home + hi + 1) >> 1;
+        if (a.cta_begin[mid] <= b) home = mid;
         else hi = mid - 1;
     }
-    const int cb = b - a.cta_begin[gi];
-    const int first = a.group_first[gi];
-    const int gcnt = a.group_first[gi + 1] - first;
-    const ViewDev *GV = a.views + first;
-    const ViewDev &V = a.views[a.group_ref[gi]];
-    const float win_lo = a.group_win[gi][0], win_hi = a.group_win[gi][1];
-    const RayBox box = grid_box(a.vol, V);
+    const int cb = b - a.cta_begin[home];
     const int tiles = a.tiles_x * a.tiles_y;
     const long long stride = a.img_stride ? a.img_stride : static_cast<long long>(a.width) * a.height;
-    float *out = a.out + first * stride;
-    uint32_t *cnt = a.samples ? a.samples + first * stride : nullptr;
-    int tile = cb * wpc + warp;
-    for (;;) {
-        if (a.persistent) {
-            int it = 0;
-            if (lane == 0) it = atomicAdd(a.queue + gi, 1);
-            tile = __shfl_sync(kFull, it, 0);
+    // home group first, then the other groups' tiles in turn (as march_kernel)
+    const int rounds = a.persistent ? a.n_groups : 1;
+    for (int r = 0; r < rounds; ++r) {
+        const int gi = home + r < a.n_groups ? home + r : home + r - a.n_groups;
+        const int first = a.group_first[gi];
+        const int gcnt = a.group_first[gi + 1] - first;
+        const ViewDev *GV = a.views + first;
+        const ViewDev &V = a.views[a.group_ref[gi]];
+        const float win_lo = a.group_win[gi][0], win_hi = a.group_win[gi][1];
+        const RayBox box = grid_box(a.vol, V);
+        float *out = a.out + first * stride;
+        uint32_t *cnt = a.samples ? a.samples + first * stride : nullptr;
+        int tile = cb * wpc + warp;
+        for (;;) {
+            if (a.persistent) {
+                int it = 0;
+                if (lane == 0) it = atomicAdd(a.queue + gi, 1);
+                tile = __shfl_sync(kFull, it, 0);
+            }
+            if (__any_sync(kFull, tile >= tiles)) break;  // uniform across the warp
+            const int tx = tile % a.tiles_x;
+            const int ty = tile / a.tiles_x;
+            const int p = tx * a.packet_w + lane % a.packet_w;
+            const int q = ty * a.packet_h + lane / a.packet_w;
+            march_group<STORE, DEPTH, PAIRED, G>(a.vol, V, win_lo, win_hi, GV, a.view_delta + first,
+                                                 a.view_dhi + first, gcnt, box, p, q, a.width, a.height, out, stride,
+                                                 cnt, a.error_word, s_tab);
+            if (!a.persistent) break;
         }
-        if (tile >= tiles) break;
-        const int tx = tile % a.tiles_x;
-        const int ty = tile / a.tiles_x;
-        const int p = tx * a.packet_w + lane % a.packet_w;
-        const int q = ty * a.packet_h + lane / a.packet_w;
-        march_group<STORE, DEPTH, PAIRED, G>(a.vol, V, win_lo, win_hi, GV, a.view_delta + first, a.view_dhi + first,
-                                             gcnt, box, p, q, a.width, a.height, out, stride, cnt, a.error_word,
-                                             s_tab);
-        if (!a.persistent) break;
     }
 }
 
@@ -1161,26 +1198,27 @@ __global__ void __launch_bounds__(256) reduce_kernel(const __grid_constant__ Red
 }
 
 template <int STORE, int DEPTH, int MINB, bool PAIRED>
-void *kernel_ptr()
+void *kernel_ptr(bool steal)
 {
-    return reinterpret_cast<void *>(&march_kernel<STORE, DEPTH, MINB, PAIRED>);
+    return steal ? reinterpret_cast<void *>(&march_kernel<STORE, DEPTH, MINB, PAIRED, true>)
+                 : reinterpret_cast<void *>(&march_kernel<STORE, DEPTH, MINB, PAIRED, false>);
 }
 
 template <int STORE, int MINB, bool PAIRED>
-void *select_depth(int depth)
+void *select_depth(int depth, bool steal)
 {
     switch (depth) {
-    case 1: return kernel_ptr<STORE, 1, MINB, PAIRED>();
-    case 2: return kernel_ptr<STORE, 2, MINB, PAIRED>();
-    case 4: return kernel_ptr<STORE, 4, MINB, PAIRED>();
+    case 1: return kernel_ptr<STORE, 1, MINB, PAIRED>(steal);
+    case 2: return kernel_ptr<STORE, 2, MINB, PAIRED>(steal);
+    case 4: return kernel_ptr<STORE, 4, MINB, PAIRED>(steal);
     default: return nullptr;
     }
 }
 
 template <int STORE, bool PAIRED>
-void *select_cap(int depth, int capped)
+void *select_cap(int depth, int capped, bool steal)
 {
-    return capped ? select_depth<STORE, 3, PAIRED>(depth) : select_depth<STORE, 1, PAIRED>(depth);
+    return capped ? select_depth<STORE, 3, PAIRED>(depth, steal) : select_depth<STORE, 1, PAIRED>(depth, steal);
 }
 
 template <int STORE, bool PAIRED>
@@ -1202,13 +1240,16 @@ void *select_group(int store, int paired, int size)
     return nullptr;
 }
 
-void *select_kernel(int store, int depth, int capped, int paired)
+// steal: persistent CTAs move on to the other views' tiles once their own
+// view's are spent (launches of more than one view).
+void *select_kernel(int store, int depth, int capped, int paired, bool steal)
 {
     if (store == GBD_STORE_F32)
-        return paired ? select_cap<GBD_STORE_F32, true>(depth, capped) : select_cap<GBD_STORE_F32, false>(depth, capped);
+        return paired ? select_cap<GBD_STORE_F32, true>(depth, capped, steal)
+                      : select_cap<GBD_STORE_F32, false>(depth, capped, steal);
     if (store == GBD_STORE_BF16_F16U)
-        return paired ? select_cap<GBD_STORE_BF16_F16U, true>(depth, capped)
-                      : select_cap<GBD_STORE_BF16_F16U, false>(depth, capped);
+        return paired ? select_cap<GBD_STORE_BF16_F16U, true>(depth, capped, steal)
+                      : select_cap<GBD_STORE_BF16_F16U, false>(depth, capped, steal);
     return nullptr;
 }
 
@@ -1352,7 +1393,8 @@ cudaError_t plan_march(MarchArgs &a, const LaunchCfg &cfg, int num_sms, const do
     // n_groups > 0: time groups, one unit of CTAs per group; else one per view
     const bool grouped = a.n_groups > 0;
     void *k = grouped ? select_group(a.vol.store, a.vol.paired, a.group_size)
-                      : select_kernel(a.vol.store, cfg.depth, cfg.regcap, a.vol.paired);
+                      : select_kernel(a.vol.store, cfg.depth, cfg.regcap, a.vol.paired,
+                                      a.persistent && a.n_views > 1);
     if (!k || a.n_views < 1 || a.n_views > kViewsPerLaunch) return cudaErrorInvalidValue;
     if (grouped && (a.n_groups > a.n_views || a.group_first[0] != 0 || a.group_first[a.n_groups] != a.n_views))
         return cudaErrorInvalidValue;
