@@ -445,6 +445,38 @@ void group_views(MarchArgs &a, int gmax)
     a.group_size = most <= 4 ? 4 : kGroupMax;
 }
 
+int launch_units(const MarchArgs &a) { return a.n_groups > 0 ? a.n_groups : a.n_views; }
+
+const int *tile_order(Ctx &ctx, int width, int height, int packet_w, int packet_h)
+{
+    const std::array<int, 4> key{width, height, packet_w, packet_h};
+    auto it = ctx.tile_orders.find(key);
+    if (it != ctx.tile_orders.end()) return it->second;
+    const int tx = (width + packet_w - 1) / packet_w, ty = (height + packet_h - 1) / packet_h;
+    std::vector<int> order(static_cast<size_t>(tx) * ty);
+    std::vector<double> d2(order.size());
+    for (int y = 0; y < ty; ++y)
+        for (int x = 0; x < tx; ++x) {
+            const double dx = (x + 0.5) * packet_w - 0.5 * width, dy = (y + 0.5) * packet_h - 0.5 * height;
+            const int t = y * tx + x;
+            order[static_cast<size_t>(t)] = t;
+            d2[static_cast<size_t>(t)] = dx * dx + dy * dy;
+        }
+    std::stable_sort(order.begin(), order.end(), [&](int p, int q) { return d2[p] < d2[q]; });
+    int *dev = nullptr;
+    if (cudaMalloc(reinterpret_cast<void **>(&dev), order.size() * sizeof(int)) != cudaSuccess) return nullptr;
+    // on the load stream (not the legacy default stream, which would wait for
+    // the caller's streams); the host vector must outlive the copy
+    if (cudaMemcpyAsync(dev, order.data(), order.size() * sizeof(int), cudaMemcpyHostToDevice, ctx.load_stream) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(ctx.load_stream) != cudaSuccess) {
+        cudaFree(dev);
+        return nullptr;
+    }
+    ctx.tile_orders[key] = dev;
+    return dev;
+}
+
 // Bytes of the per-view tile counters of a batch, rounded up to 256.
 static size_t queue_bytes(int n) { return (static_cast<size_t>(n) * sizeof(int) + 255) / 256 * 256; }
 
@@ -636,6 +668,8 @@ int render_direct(Ctx &ctx, const Volume &vol, const std::vector<ViewDev> &hv, c
         fill_args(*a, vol, hv.data(), n, c, spec, dev_out, spec.out_on_host ? nullptr : spec.samples, queue, cfg,
                   ctx.err_word);
         group_views(*a, cfg.group);
+        if (cfg.persistent && launch_units(*a) == 1)
+            a->tile_order = tile_order(ctx, spec.width, spec.height, cfg.packet_w, cfg.packet_h);
         e = launch_march(*a, cfg, ctx.num_sms, work.data() + static_cast<size_t>(c) * kViewsPerLaunch, st);
     }
     if (e == cudaSuccess && spec.out_on_host)
@@ -721,6 +755,8 @@ static cudaError_t chunk_params(Ctx &ctx, const Volume &vol, const GraphKey &key
     fill_args(a, vol, hv, key.n, c, spec, dev_out, spec.out_on_host ? nullptr : spec.samples, queue, key.cfg,
               ctx.err_word);
     group_views(a, key.cfg.group);
+    if (key.cfg.persistent && launch_units(a) == 1)
+        a.tile_order = tile_order(ctx, spec.width, spec.height, key.cfg.packet_w, key.cfg.packet_h);
     double work[kViewsPerLaunch];
     for (int v = 0; v < a.n_views; ++v) work[v] = view_work(vol, a.views[v], spec.width, spec.height);
     KernelLaunch L;
@@ -998,6 +1034,8 @@ int gbd_destroy(gbd_ctx *ctx)
         }
         ctx->volumes.clear();
         if (ctx->err_word) cudaFree(ctx->err_word);
+        for (auto &kv : ctx->tile_orders) cudaFree(kv.second);
+        ctx->tile_orders.clear();
         if (ctx->load_stream) cudaStreamDestroy(ctx->load_stream);
         if (ctx->capture_stream) cudaStreamDestroy(ctx->capture_stream);
         for (int k = 0; k < 4; ++k) {

@@ -114,6 +114,7 @@ struct MarchArgs {
     float *out;               // n_views * width * height floats
     uint32_t *samples;        // optional, same shape
     int *queue;               // persistent mode: one tile counter per view or group (zeroed before launch)
+    const int *tile_order;    // persistent mode: counter value -> tile (centre of the image first), or NULL
     int *error_word;          // checked builds: first bounds violation code
     // vector renders (vector_kernel): extra emissivity channels of the volume
     const float *chan;        // n_chan channels, each M blocks of chan_cell_stride floats

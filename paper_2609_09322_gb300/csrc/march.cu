@@ -893,6 +893,7 @@ __global__ void __launch_bounds__(256, MINB) march_kernel(const __grid_constant_
                     tile = __shfl_sync(kFull, it, 0);
                 }
                 if (__any_sync(kFull, tile >= tiles)) break;
+                if (a.persistent && a.tile_order) tile = __ldg(a.tile_order + tile);
                 const int tx = tile % a.tiles_x;
                 const int ty = tile / a.tiles_x;
                 const int p = tx * a.packet_w + lane % a.packet_w;
@@ -916,6 +917,7 @@ __global__ void __launch_bounds__(256, MINB) march_kernel(const __grid_constant_
                 tile = __shfl_sync(kFull, it, 0);
             }
             if (tile >= tiles) break;
+            if (a.persistent && a.tile_order) tile = __ldg(a.tile_order + tile);
             const int p = (tile % a.tiles_x) * a.packet_w + lane % a.packet_w;
             const int q = (tile / a.tiles_x) * a.packet_h + lane / a.packet_w;
             march_ray<STORE, DEPTH, PAIRED, true>(a.vol, V, box, p, q, a.width, a.height, out, cnt, a.error_word,
@@ -972,6 +974,7 @@ __global__ void __launch_bounds__(256, 3) group_kernel(const __grid_constant__ M
                 tile = __shfl_sync(kFull, it, 0);
             }
             if (__any_sync(kFull, tile >= tiles)) break;  // uniform across the warp
+            if (a.persistent && a.tile_order) tile = __ldg(a.tile_order + tile);
             const int tx = tile % a.tiles_x;
             const int ty = tile / a.tiles_x;
             const int p = tx * a.packet_w + lane % a.packet_w;

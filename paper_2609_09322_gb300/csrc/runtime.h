@@ -6,6 +6,7 @@
 #include <atomic>
 #include <cstdint>
 #include <cstring>
+#include <array>
 #include <map>
 #include <memory>
 #include <mutex>
@@ -67,6 +68,7 @@ struct gbd_ctx {
     gbd::GraphCache *graphs = nullptr;
     gbd::Server *server = nullptr;
     std::map<gbd::TuneKey, gbd::TuneEntry> tuned;
+    std::map<std::array<int, 4>, int *> tile_orders;  // device tables of tile_order(), by image and packet shape
     ~gbd_ctx();
     gbd::Volume *find(gbd_volume id);
 };
@@ -117,6 +119,15 @@ void fill_args(MarchArgs &a, const Volume &vol, const ViewDev *hv, int n, int c,
                float *out, uint32_t *samples, int *queue, const LaunchCfg &cfg, int *err_word);
 // Time groups of a filled launch (batched renders; see MarchArgs).
 void group_views(MarchArgs &a, int gmax);
+// The order in which persistent warps take a view's tiles: by distance of the
+// tile from the image centre, nearest first (the longest rays of a centred
+// box first, so the launch ends on short ones).  A device table cached in the
+// context; NULL (counter order) if it cannot be made.  Used by launches of one
+// view or time group; with several, warps move on to the other views' tiles
+// instead, and counter order keeps neighbouring warps on neighbouring tiles.
+const int *tile_order(Ctx &ctx, int width, int height, int packet_w, int packet_h);
+// Views, or time groups when grouped, of a filled launch.
+int launch_units(const MarchArgs &a);
 bool build_layout(const int n[3], int B, int S, std::vector<int32_t> &tab, long long &epoch_stride, int morton_cells);
 void destroy_graph_cache(GraphCache *g);
 

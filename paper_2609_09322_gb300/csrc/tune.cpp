@@ -93,6 +93,8 @@ int time_config(Ctx &ctx, const Volume &vol, const std::vector<ViewDev> &hv, con
             fill_args(*args, vol, hv.data(), n, c, spec, spec.out, nullptr, reinterpret_cast<int *>(scratch), cfg,
                       ctx.err_word);
             group_views(*args, cfg.group);
+            if (cfg.persistent && launch_units(*args) == 1)
+                args->tile_order = tile_order(ctx, spec.width, spec.height, cfg.packet_w, cfg.packet_h);
             e = launch_march(*args, cfg, ctx.num_sms, work.data() + static_cast<size_t>(c) * kViewsPerLaunch, st);
         }
         if (e == cudaSuccess) e = cudaEventRecord(b, st);
