@@ -1000,33 +1000,38 @@ __global__ void __launch_bounds__(256, MINB) vector_kernel(const __grid_constant
     const int warp = threadIdx.x >> 5;
     const int wpc = blockDim.x >> 5;
     const int b = static_cast<int>(blockIdx.x);
-    int vi = 0, hi = a.n_views - 1;
-    while (vi < hi) {
-        const int mid = (vi + hi + 1) >> 1;
-        if (a.cta_begin[mid] <= b) vi = mid;
+    int home = 0, hi = a.n_views - 1;
+    while (home < hi) {
+        const int mid = (home + hi + 1) >> 1;
+        if (a.cta_begin[mid] <= b) home = mid;
         else hi = mid - 1;
     }
-    const int cb = b - a.cta_begin[vi];
-    const ViewDev &V = a.views[vi];
-    const RayBox box = grid_box(a.vol, V);
+    const int cb = b - a.cta_begin[home];
     const int tiles = a.tiles_x * a.tiles_y;
-    float *out = a.out + static_cast<long long>(vi) * a.img_stride;
     const ChanPtrs ch{a.chan, a.chan_comp_stride, a.chan_cell_stride};
-    int tile = cb * wpc + warp;
-    for (;;) {
-        if (a.persistent) {
-            int it = 0;
-            if (lane == 0) it = atomicAdd(a.queue + vi, 1);
-            tile = __shfl_sync(kFull, it, 0);
+    // home view first, then the other views' tiles in turn (as march_kernel)
+    const int rounds = a.persistent ? a.n_views : 1;
+    for (int r = 0; r < rounds; ++r) {
+        const int vi = home + r < a.n_views ? home + r : home + r - a.n_views;
+        const ViewDev &V = a.views[vi];
+        const RayBox box = grid_box(a.vol, V);
+        float *out = a.out + static_cast<long long>(vi) * a.img_stride;
+        int tile = cb * wpc + warp;
+        for (;;) {
+            if (a.persistent) {
+                int it = 0;
+                if (lane == 0) it = atomicAdd(a.queue + vi, 1);
+                tile = __shfl_sync(kFull, it, 0);
+            }
+            if (__any_sync(kFull, tile >= tiles)) break;  // uniform across the warp
+            const int tx = tile % a.tiles_x;
+            const int ty = tile / a.tiles_x;
+            const int p = tx * a.packet_w + lane % a.packet_w;
+            const int q = ty * a.packet_h + lane / a.packet_w;
+            march_ray<STORE, 2, PAIRED, true, false, NCH>(a.vol, V, box, p, q, a.width, a.height, out, nullptr,
+                                                           a.error_word, s_tab, false, ch);
+            if (!a.persistent) break;
         }
-        if (tile >= tiles) break;
-        const int tx = tile % a.tiles_x;
-        const int ty = tile / a.tiles_x;
-        const int p = tx * a.packet_w + lane % a.packet_w;
-        const int q = ty * a.packet_h + lane / a.packet_w;
-        march_ray<STORE, 2, PAIRED, true, false, NCH>(a.vol, V, box, p, q, a.width, a.height, out, nullptr,
-                                                       a.error_word, s_tab, false, ch);
-        if (!a.persistent) break;
     }
 }
 
