@@ -452,6 +452,7 @@ const int *tile_order(Ctx &ctx, int width, int height, int packet_w, int packet_
     const std::array<int, 4> key{width, height, packet_w, packet_h};
     auto it = ctx.tile_orders.find(key);
     if (it != ctx.tile_orders.end()) return it->second;
+    if (ctx.tile_orders.size() >= 64) return nullptr;  // bounded: further geometries keep counter order
     const int tx = (width + packet_w - 1) / packet_w, ty = (height + packet_h - 1) / packet_h;
     std::vector<int> order(static_cast<size_t>(tx) * ty);
     std::vector<double> d2(order.size());

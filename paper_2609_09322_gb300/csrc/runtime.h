@@ -122,7 +122,8 @@ void group_views(MarchArgs &a, int gmax);
 // The order in which persistent warps take a view's tiles: by distance of the
 // tile from the image centre, nearest first (the longest rays of a centred
 // box first, so the launch ends on short ones).  A device table cached in the
-// context; NULL (counter order) if it cannot be made.  Used by launches of one
+// context for up to 64 image geometries; NULL (counter order) beyond them or
+// if it cannot be made.  Used by launches of one
 // view or time group; with several, warps move on to the other views' tiles
 // instead, and counter order keeps neighbouring warps on neighbouring tiles.
 const int *tile_order(Ctx &ctx, int width, int height, int packet_w, int packet_h);
