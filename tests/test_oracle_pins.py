@@ -236,6 +236,40 @@ def test_brute_force_fine_steps(lookback, beaming):
     assert checked >= 3
 
 
+@pytest.mark.parametrize("split", [False, True])
+def test_pixel_list_equals_whole_image(split):
+    """The pixel-list entry point (used for sampled checks of full-size
+    images) takes its pairs as (p, q) = (column, row): on a non-square image,
+    a random anisotropic grid with lookback and beaming, every listed pixel
+    equals the whole-image render at [q, p] bit for bit, counts included, in
+    any order and with repeats; pixels off the image give 0 and no samples."""
+    rng = np.random.default_rng(11)
+    M = 4
+    grid = gen.Grid(n=(9, 6, 7), origin=(1.5, -2.0, 0.25), dx=(0.7, 1.2, 1.0), n_epochs=M, t0=0.3, dt=1.9)
+    nx, ny, nz = grid.n
+    j = rng.random((M, nz, ny, nx)) + 0.05
+    d = rng.normal(size=(M, nz, ny, nx, 3))
+    d /= np.linalg.norm(d, axis=-1, keepdims=True)
+    beta = d * rng.uniform(0.0, 0.9, size=(M, nz, ny, nx, 1))
+    v = gen.view_from_angles(grid, 57.0, 23.0, size=13, c=1.3, t_obs=3.1, nu_ratio=1.7).with_(
+        height=9, fov_v=gen.view_from_angles(grid, 57.0, 23.0, size=13).fov_v * 9 / 13)
+    img, cnt = oracle.render(grid, j, beta, v, counts=True, split_at_nodes=split)
+    assert np.count_nonzero(img) > img.size // 2
+    pq = [(p, q) for q in range(v.height) for p in range(v.width)]
+    sel = rng.permutation(len(pq))
+    listed = np.array([pq[k] for k in sel] + [pq[k] for k in sel[:40]], dtype=np.int32)
+    val, c = oracle.render_pixels(grid, j, beta, v, listed, counts=True, split_at_nodes=split)
+    want = img[listed[:, 1], listed[:, 0]]
+    assert np.array_equal(val, want)
+    assert np.array_equal(c, cnt[listed[:, 1], listed[:, 0]])
+    # the transposed reading would differ: the image is not symmetric
+    assert not np.array_equal(img[: v.height, : v.height], img[: v.height, : v.height].T)
+    off = np.array([(-1, 0), (0, -1), (v.width, 0), (0, v.height), (v.width + 5, v.height + 5),
+                    (-(2 ** 31), 3), (3, 2 ** 31 - 1)], dtype=np.int32)
+    val, c = oracle.render_pixels(grid, j, beta, v, off, counts=True, split_at_nodes=split)
+    assert np.all(val == 0.0) and np.all(c == 0)
+
+
 def test_midpoint_equals_split_without_node_crossings():
     """With the fields read at one epoch coordinate per chord, the chord
     midpoint is exact whenever no chord crosses an epoch node; fast light is
