@@ -254,9 +254,17 @@ int gbd_render_batch(gbd_ctx *ctx, gbd_volume vol, const gbd_view *views, int32_
  *  - at most GBD_NOALLOC_MAX_VIEWS views per call, otherwise GBD_ERR_INVALID;
  *  - spec->out (and spec->samples, if set) must be device memory;
  *    out_on_host is rejected with GBD_ERR_INVALID;
+ *  - the whole-ray march only: an explicit launch with region != 0 is
+ *    rejected with GBD_ERR_INVALID, and a tuned region schedule is replaced
+ *    by the persistent whole-ray march with the tuned packet, CTA and group
+ *    shapes (its images then agree with gbd_render_batch's to float32
+ *    rounding, as any region render does); tiles are taken in counter order,
+ *    never from the centre-first order table (which would need an allocation);
+ *    otherwise the images equal gbd_render_batch's bit for bit;
  *  - the first call on a device looks up the array's device address on that
- *    device (cudaGetSymbolAddress); make that first call before any stream
- *    capture;
+ *    device (cudaGetSymbolAddress) and keeps it for the life of the process;
+ *    make that first call before any stream capture, and do not use this entry
+ *    point on a device after a cudaDeviceReset there;
  *  - every call shares the one array, which keeps the last call's contents
  *    (the tile counters are cleared by each call): calls whose GPU work overlaps,
  *    from any context or stream on the same device, race on it, so the caller
@@ -373,7 +381,11 @@ typedef struct {
     int32_t max_requests_per_wave;   /* default 256, at most 4096                       */
     int32_t max_requests_in_flight;  /* request slots (default 1024)                    */
     uint64_t request_budget_bytes;   /* device bytes for running requests; 0 = what the
-                                        volumes leave of the context budget              */
+                                        volumes leave of the context budget.  Each
+                                        request is charged its image (4 B per pixel,
+                                        twice with device sample counts): a device
+                                        buffer of the library's for host output, the
+                                        caller's own buffer for device output      */
     gbd_launch launch;               /* wave kernel configuration (depth 1 or 2); all
                                         zero: packet 8x4, 4 warps, depth 2, capped
                                         registers                                 */

@@ -35,7 +35,10 @@ MarchArgs g_args;                         // launch arguments (about 28 KB: not 
 double g_work[kViewsPerLaunch];           // per-view work estimates of one launch
 
 // Looks up the device address of the scratch array on the current device
-// (once per device; the caller holds g_mu and has made `dev` current).
+// (once per device; the caller holds g_mu and has made `dev` current).  The
+// address is kept for the life of the process: a cudaDeviceReset, which
+// tears down the context the address belongs to, ends this entry point's use
+// on that device.
 int scratch_address(int dev, char **out)
 {
     if (dev < 0 || dev >= kMaxDevices) return fail(GBD_ERR_INVALID, "device index %d not supported here", dev);
@@ -68,10 +71,20 @@ extern "C" int gbd_render_batch_noalloc(gbd_ctx *ctx, gbd_volume vid, const gbd_
     LaunchCfg cfg = resolve_launch(launch);
     int rc = check_launch(cfg);
     if (rc) return rc;
+    // The region schedule needs partial-sum slots that grow with the batch;
+    // this entry point has no room for them.
+    if (cfg.region != 0)
+        return fail(GBD_ERR_INVALID, "gbd_render_batch_noalloc has no region schedule (launch.region must be 0)");
     std::lock_guard<std::mutex> lock(ctx->mu);
     Volume *vol = ctx->find(vid);
     if (!vol) return fail(GBD_ERR_NOTFOUND, "unknown volume %llu", static_cast<unsigned long long>(vid));
-    if (!launch) lookup_tuned(*ctx, tune_key(*vol, spec->width, spec->height, n, views[0].flags), cfg);
+    if (!launch) {
+        // a tuned region schedule is replaced by the whole-ray march (the
+        // tuned packet, CTA and group shapes are kept)
+        lookup_tuned(*ctx, tune_key(*vol, spec->width, spec->height, n, views[0].flags), cfg);
+        cfg.region = 0;
+        cfg.persistent = 1;
+    }
     DeviceGuard guard(ctx->device);
 
     std::lock_guard<std::mutex> slock(g_mu);

@@ -43,7 +43,7 @@ struct ServedReq {
     ViewDev view{};
     gbd_image_spec spec{};
     int32_t priority = 0;
-    uint64_t bytes = 0;        // device bytes the library holds for it while running
+    uint64_t bytes = 0;        // device bytes its image (and counts) occupy while it runs
     int state = kPending;
     int status = GBD_OK;
     bool cancel_requested = false;
@@ -433,7 +433,11 @@ int gbd_submit(gbd_ctx *ctx, const gbd_request *req, uint64_t *ticket)
     }
     ServedReq r;
     if ((rc = make_view(*vol, req->view, sp.width, sp.height, sp.fov_u, sp.fov_v, r.view))) return rc;
-    r.bytes = sp.out_on_host ? static_cast<uint64_t>(sp.width) * sp.height * 4 : 0;
+    // A running request's HBM footprint is the image it writes: a device
+    // buffer of the library's when the output is host memory, the caller's own
+    // buffer (and its sample counts) when it is device memory.
+    const uint64_t img_bytes = static_cast<uint64_t>(sp.width) * sp.height * 4;
+    r.bytes = img_bytes + (!sp.out_on_host && sp.samples ? img_bytes : 0);
     if (r.bytes > s.request_budget)
         return fail(GBD_ERR_BUDGET, "request needs %llu device bytes, the serving budget is %llu",
                     static_cast<unsigned long long>(r.bytes), static_cast<unsigned long long>(s.request_budget));

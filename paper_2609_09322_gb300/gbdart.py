@@ -467,8 +467,24 @@ class Context:
     def render_batch_noalloc(self, vol: int, views, out, *, launch=None, stream=None):
         """``render_batch`` into the caller's device tensor ``out`` [n][H][W]
         without any allocation by the library (its scratch is a fixed
-        device array; at most 1024 views per call)."""
+        device array; at most 1024 views per call).  ``out`` must be a
+        contiguous float32 tensor of shape [n][H][W] on this context's device:
+        the library writes n * H * W floats from its first element."""
+        import torch
         views = list(views)
+        if not views:
+            raise ValueError("render_batch_noalloc needs at least one view")
+        v0 = views[0]
+        for v in views[1:]:
+            if (v.width, v.height, v.fov_u, v.fov_v) != (v0.width, v0.height, v0.fov_u, v0.fov_v):
+                raise ValueError("render_batch_noalloc needs one image geometry for all views")
+        shape = (len(views), int(v0.height), int(v0.width))
+        if not isinstance(out, torch.Tensor) or out.dtype != torch.float32 or not out.is_contiguous():
+            raise ValueError("render_batch_noalloc writes into a contiguous float32 torch tensor")
+        if out.device != torch.device("cuda", self.device):
+            raise ValueError(f"out must be on cuda:{self.device}, not {out.device}")
+        if tuple(out.shape) != shape:
+            raise ValueError(f"out must have shape {shape}, not {tuple(out.shape)}")
         arr = (CView * len(views))(*[_cview(v) for v in views])
         spec = self._spec(views[0], out.data_ptr(), None)
         rc = self.lib.gbd_render_batch_noalloc(self.handle, int(vol), arr, len(views), ctypes.byref(spec),
