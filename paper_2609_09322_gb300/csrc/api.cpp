@@ -272,6 +272,7 @@ VolDev vol_dev(const Volume &v)
     d.M = v.grid.n_epochs;
     d.store = v.store;
     d.paired = v.paired;
+    d.plain_boost = v.plain_boost;
     return d;
 }
 
@@ -1128,22 +1129,28 @@ int gbd_load_snapshots(gbd_ctx *ctx, const gbd_grid *grid, const gbd_fields *f, 
         pa.m = m;
         pa.paired = vol->paired;
         pa.bad = bad;
+        pa.gamma2_max = reinterpret_cast<unsigned *>(bad) + 1;
         if (e == cudaSuccess) e = launch_pack(pa, st);
         // The host staging buffer is reused for the next epoch only after
         // this epoch's pack has consumed it.
         if (e == cudaSuccess && !f->on_device) e = cudaStreamSynchronize(st);
     }
-    int h_bad = 0;
-    if (e == cudaSuccess) e = cudaMemcpyAsync(&h_bad, bad, sizeof(int), cudaMemcpyDeviceToHost, st);
+    int h_bad[2] = {0, 0};
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h_bad, bad, 2 * sizeof(int), cudaMemcpyDeviceToHost, st);
     if (stage) cudaFreeAsync(stage, st);
     if (bad) cudaFreeAsync(bad, st);
     cudaError_t es = cudaStreamSynchronize(st);
     if (e == cudaSuccess) e = es;
     if (e != cudaSuccess) { cleanup(); return cuda_fail(e, "volume pack"); }
-    if (h_bad) {
+    if (h_bad[0]) {
         cleanup();
         return fail(GBD_ERR_INVALID, "fields: negative or non-finite j', non-finite beta, or |beta| >= 1 "
                                      "(float32 storage needs |beta|^2 <= 1 - 2^-20)");
+    }
+    if (f->store == GBD_STORE_BF16_F16U) {
+        float g2 = 0.f;
+        std::memcpy(&g2, &h_bad[1], sizeof(g2));
+        vol->plain_boost = g2 <= kPlainGamma2 ? 1 : 0;
     }
     vol->bytes = bytes + tab_bytes;
     ctx->used += vol->bytes;
@@ -1263,13 +1270,13 @@ int gbd_load_channels(gbd_ctx *ctx, gbd_volume vid, const void *chans, int32_t n
             if (e == cudaSuccess) e = launch_chan_pack(pa, st);
             if (e == cudaSuccess && !on_device) e = cudaStreamSynchronize(st);  // the stage takes the next epoch
         }
-    int h_bad = 0;
-    if (e == cudaSuccess) e = cudaMemcpyAsync(&h_bad, bad, sizeof(int), cudaMemcpyDeviceToHost, st);
+    int h_bad[2] = {0, 0};
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h_bad, bad, 2 * sizeof(int), cudaMemcpyDeviceToHost, st);
     if (stage) cudaFreeAsync(stage, st);
     if (bad) cudaFreeAsync(bad, st);
     cudaError_t es = cudaStreamSynchronize(st);
     if (e == cudaSuccess) e = es;
-    if (e != cudaSuccess || h_bad) {
+    if (e != cudaSuccess || h_bad[0]) {
         cudaFree(dst);
         if (e != cudaSuccess) return cuda_fail(e, "channel pack");
         return fail(GBD_ERR_INVALID, "channels: non-finite value");

@@ -30,7 +30,13 @@ struct VolDev {
     int M;
     int store;                // GBD_STORE_*
     int paired;               // 1: block b holds snapshots b-1 and b side by side
+    int plain_boost;          // bfloat16/float16 records whose Gamma^2 = 1 + |u|^2 <= kPlainGamma2:
+                              // the march may take D = 1 / (Gamma + u.s_hat) as it stands
 };
+
+// Largest Gamma^2 of a bfloat16/float16 volume whose march evaluates the
+// Doppler factor in the plain form (Gamma <= 8, beta <= 0.992).
+constexpr float kPlainGamma2 = 64.0f;
 
 // March tables.  The march steps every axis towards increasing cell index:
 // an axis the view runs down is mirrored (cell k' = n - 1 - k) on the host.
@@ -40,6 +46,8 @@ struct VolDev {
 // sentinel tells the march so; the second sentinel absorbs the read-ahead
 // of the next cell's term.
 constexpr int32_t kTabSentinel = INT32_MIN;
+// Sentinels after the last staged table in shared memory (see stage_tables).
+constexpr int kTabPad = 2;
 __host__ __device__ inline int march_table_base(const int n[3], int axis)
 {
     return axis == 0 ? 0 : (axis == 1 ? 2 * (n[0] + 2) : 2 * (n[0] + 2) + 2 * (n[1] + 2));
@@ -238,6 +246,8 @@ struct PackArgs {
     int m;                    // epoch being packed
     int paired;               // write into blocks m (second slot) and m + 1 (first slot)
     int *bad;                 // device flag: set to 1 on an invalid value
+    unsigned *gamma2_max;     // bfloat16/float16 store: atomic max of the bits of the stored
+                              // records' Gamma^2 = 1 + |u|^2 (a non-negative float); may be NULL
 };
 cudaError_t launch_pack(const PackArgs &a, cudaStream_t stream);
 

@@ -26,6 +26,14 @@
 // Time groups (batched renders of one direction at several observer times):
 // one traversal per ray serves up to 4 or 8 views, each with its own sums
 // (march_group, group_kernel).
+//
+// bfloat16/float16 records (march_ray_bf16, march_group_bf16) take a lighter
+// march whose storage error (2^-9 in j', 2^-11 in u) dwarfs its arithmetic:
+// the epoch coordinate is a float linear in s instead of the exact fixed
+// point, the step runs without branches for every lane (a lane whose ray has
+// ended takes no step and reads nothing), the Doppler factor is the plain
+// 1 / (Gamma + u.s_hat) where the volume's Gamma allows it, and the sum is
+// not compensated.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -69,6 +77,7 @@ struct BoostConsts {
     float slx, sly, slz;  // rounding residual of s_hat
     float expo;           // 2 - alpha
     bool beaming;
+    bool plain;           // bfloat16/float16 records: D = 1 / (Gamma + u.s_hat) (volume's Gamma <= 8)
 };
 
 template <int STORE>
@@ -133,6 +142,14 @@ struct Record<GBD_STORE_BF16_F16U> {
         lo = make_uint2(v.x, v.y);
         hi = make_uint2(v.z, v.w);
     }
+    // The same by byte address.
+    static __device__ __forceinline__ T load_at(unsigned long long a) { return __ldg(reinterpret_cast<const uint2 *>(a)); }
+    static __device__ __forceinline__ void load_pair_at(unsigned long long a, T &lo, T &hi)
+    {
+        const uint4 v = __ldg(reinterpret_cast<const uint4 *>(a));
+        lo = make_uint2(v.x, v.y);
+        hi = make_uint2(v.z, v.w);
+    }
     // D = 1 / (Gamma + u.s_hat).  When u.s_hat < 0 (motion towards the
     // observer) the denominator cancels, so the same D is evaluated as
     // (Gamma + |u.s_hat|) / (1 + |u|^2 - (u.s_hat)^2), which has no cancellation.
@@ -160,6 +177,30 @@ struct Record<GBD_STORE_BF16_F16U> {
     static __device__ __forceinline__ float boosted(const T r, const BoostConsts &c)
     {
         return emissivity(r) * boost(r, c);
+    }
+    // boosted2() in the plain form D = 1 / (Gamma + u.s_hat), log2 D =
+    // -log2(Gamma + u.s_hat).  For u.s_hat near -Gamma the sum cancels: its
+    // float32 rounding (about 3.3e-7 Gamma absolute) over Gamma + u.s_hat >=
+    // 1 / (2 Gamma) bounds the relative error of D by 6.6e-7 Gamma^2, at most
+    // 4.3e-5 (1.1e-4 in D^2.6) for Gamma <= 8, the volumes this form is used
+    // for (beta <= 0.992); the float16 u itself carries 4.9e-4.
+    static __device__ __forceinline__ float2 boosted2_plain(const T lo, const T hi, const BoostConsts &c)
+    {
+        const float2 j = make_float2(__uint_as_float(lo.x << 16), __uint_as_float(hi.x << 16));
+        if (!c.beaming) return j;
+        const uint32_t px = __byte_perm(lo.x, hi.x, 0x7632);  // (u_x lo, u_x hi)
+        const uint32_t py = __byte_perm(lo.y, hi.y, 0x5410);  // (u_y lo, u_y hi)
+        const uint32_t pz = __byte_perm(lo.y, hi.y, 0x7632);  // (u_z lo, u_z hi)
+        __half2 hx, hy, hz;
+        memcpy(&hx, &px, sizeof(hx));
+        memcpy(&hy, &py, sizeof(hy));
+        memcpy(&hz, &pz, sizeof(hz));
+        const float2 ux = __half22float2(hx), uy = __half22float2(hy), uz = __half22float2(hz);
+        const float2 us = __ffma2_rn(ux, f2(c.shx), __ffma2_rn(uy, f2(c.shy), __fmul2_rn(uz, f2(c.shz))));
+        const float2 g2 = __ffma2_rn(ux, ux, __ffma2_rn(uy, uy, __ffma2_rn(uz, uz, f2(1.0f))));  // Gamma^2
+        const float2 den = __fadd2_rn(make_float2(sqrt_approx(g2.x), sqrt_approx(g2.y)), us);
+        const float2 e = __fmul2_rn(f2(-c.expo), make_float2(lg2_approx(den.x), lg2_approx(den.y)));
+        return __fmul2_rn(j, make_float2(ex2_approx(e.x), ex2_approx(e.y)));
     }
     // boosted() of two records at once: their u components are paired by
     // byte permutes, then each lane takes the same correctly rounded steps as
@@ -235,6 +276,14 @@ __device__ __forceinline__ int32_t tab_at(const int32_t *base, uint32_t cur)
     const int32_t *p = reinterpret_cast<const int32_t *>(reinterpret_cast<const char *>(base) + cur);
     if (SMEM) return *p;
     return __ldg(p);
+}
+
+// Copies a volume's march tables into shared memory, followed by kTabPad
+// sentinels: the branch-free step of a lane whose ray has ended reads up to
+// two entries past the sentinel pair it stopped at.
+__device__ __forceinline__ void stage_tables(int32_t *s_tab, const int32_t *src, int ntab)
+{
+    for (int i = threadIdx.x; i < ntab + kTabPad; i += blockDim.x) s_tab[i] = i < ntab ? src[i] : kTabSentinel;
 }
 
 // State of one axis of a ray: the next face crossing and what changes there.
@@ -313,6 +362,7 @@ struct RayState {
     AxisState ax[3];
     float s_cur;       // s of the latest face crossed
     long long u_cur;   // epoch coordinate there, Q31.32
+    long long u_a;     // epoch coordinate at the anchor (s = 0), Q31.32
     bool alive;
 #ifdef GBD_CHECKED
     int kc[3], kd[3];  // current cell in the volume's own frame, and its step per axis
@@ -369,6 +419,7 @@ __device__ __forceinline__ void setup_ray(RayState &R, const VolDev &vol, const 
     // the face spacing along the ray (inv_a, Eq. 11), so that the crossing of
     // the plane nk cells above the cell's lower face is at nk inv_a - o inv_a.
     const long long u_a = V.u_obs - dd_mul_fix(sa, V.kk_hi, V.kk_lo, kTwo32);
+    R.u_a = u_a;
     s_cur = -3.0e38f;  // the latest entry face of the anchor cell
     u_cur = 0;
 #pragma unroll
@@ -443,6 +494,307 @@ __device__ __forceinline__ void setup_ray(RayState &R, const VolDev &vol, const 
     }
 }
 
+// The float epoch coordinate of the bfloat16/float16 march: u(s) = c0 -
+// kk s along the ray (s from the anchor), so that the chord midpoint's is
+// c0 + mkk (s_cur + s_exit) with mkk = -kk / 2; the ray has passed the last
+// time that reaches a snapshot (u < -1) beyond s_stop.  c0 is the exact
+// coordinate at the anchor rounded to float: the coordinate is off by at most
+// a few float ulps of M (2e-6 snapshots at M = 16), against the 2^-9 and
+// 2^-11 resolution of the stored j' and u.
+struct EpochLine {
+    float c0, mkk, s_stop;
+};
+__device__ __forceinline__ EpochLine epoch_line(const RayState &R, const ViewDev &V)
+{
+    EpochLine L;
+    const float kk = V.kk_hi;
+    L.c0 = fix_to_float(R.u_a, 1.0f / kTwo32);
+    L.mkk = -0.5f * kk;
+    L.s_stop = kk > 0.f ? (L.c0 + 1.0f) / kk : 3.0e38f;
+    return L;
+}
+
+// One step of the bfloat16/float16 march through the face of axis 0, 1 or 2
+// (x0, x1, x2, at most one of them set; none once the ray has ended): the
+// plane count and crossing of that axis, and its table terms.  Every lane
+// executes it; a lane that takes no step changes nothing, and its read of
+// the table stays within the padding after the last sentinel.
+template <bool SMEM>
+__device__ __forceinline__ void step_lite(AxisState (&ax)[3], bool x0, bool x1, bool x2, float ia0, float ia1,
+                                          float ia2, const int32_t *tab)
+{
+    const uint32_t ce = x0 ? ax[0].cur : (x1 ? ax[1].cur : ax[2].cur);
+    const int32_t tn = tab_at<SMEM>(tab, ce + 8u);
+    ax[0].nkf = x0 ? ax[0].nkf + 1.0f : ax[0].nkf;
+    ax[1].nkf = x1 ? ax[1].nkf + 1.0f : ax[1].nkf;
+    ax[2].nkf = x2 ? ax[2].nkf + 1.0f : ax[2].nkf;
+    ax[0].o = x0 ? ax[0].pn : ax[0].o;
+    ax[1].o = x1 ? ax[1].pn : ax[1].o;
+    ax[2].o = x2 ? ax[2].pn : ax[2].o;
+    ax[0].pn = x0 ? tn : ax[0].pn;
+    ax[1].pn = x1 ? tn : ax[1].pn;
+    ax[2].pn = x2 ? tn : ax[2].pn;
+    ax[0].cur = x0 ? ax[0].cur + 4u : ax[0].cur;
+    ax[1].cur = x1 ? ax[1].cur + 4u : ax[1].cur;
+    ax[2].cur = x2 ? ax[2].cur + 4u : ax[2].cur;
+    ax[0].sn = fmaf(ax[0].nkf, ia0, -ax[0].of);
+    ax[1].sn = fmaf(ax[1].nkf, ia1, -ax[1].of);
+    ax[2].sn = fmaf(ax[2].nkf, ia2, -ax[2].of);
+}
+
+// The march of march_ray for bfloat16/float16 records (see the file
+// header): same cells, chords, midpoints and hat weights (Eqs. 2, 6-9, 19),
+// with the epoch coordinate of EpochLine.  PLAIN: the Doppler factor in the
+// plain form (volumes whose Gamma <= 8).
+template <int DEPTH, bool PAIRED, bool PARTIAL, bool PLAIN>
+__device__ __forceinline__ void march_ray_bf16(const VolDev &vol, const ViewDev &V, const RayBox &B, int p, int q,
+                                               int width, int height, float *out_img, uint32_t *cnt_img,
+                                               int *err_word, const int32_t *__restrict__ tab, bool accumulate)
+{
+    using Rec = Record<GBD_STORE_BF16_F16U>;
+    const bool in_image = (p < width) && (q < height);
+    RayState R;
+    setup_ray<true>(R, vol, V, B, p, q, in_image, V.win_lo, V.win_hi, tab);
+    AxisState (&ax)[3] = R.ax;
+    bool alive = R.alive;
+    float s_cur = R.s_cur;
+    const float ia0 = V.inv_a[0], ia1 = V.inv_a[1], ia2 = V.inv_a[2];
+    const EpochLine L = epoch_line(R, V);
+    const int M = vol.M;
+#ifdef GBD_CHECKED
+    int (&kc)[3] = R.kc;
+    const int kd0 = R.kd[0], kd1 = R.kd[1], kd2 = R.kd[2];
+#endif
+
+    BoostConsts bc;
+    bc.shx = V.sh_hi[0]; bc.shy = V.sh_hi[1]; bc.shz = V.sh_hi[2];
+    bc.slx = V.sh_lo[0]; bc.sly = V.sh_lo[1]; bc.slz = V.sh_lo[2];
+    bc.expo = V.expo;
+    bc.beaming = (V.flags & GBD_BEAMING) != 0u;
+    bc.plain = PLAIN;
+
+    // block b starts at byte recb + b es_bytes; a cell's record (paired: its
+    // record pair) is kUnit bytes at its layout offset
+    constexpr unsigned long long kUnit = PAIRED ? 16ull : 8ull;
+    const unsigned long long recb = reinterpret_cast<unsigned long long>(vol.rec);
+    const long long es_bytes = vol.epoch_stride * 8LL;
+
+    float acc = 0.f;
+    uint32_t count = 0;
+    while (__any_sync(kFull, alive)) {
+        unsigned long long pa[DEPTH];
+        float wgt[DEPTH], dsv[DEPTH];
+        bool has_lo[DEPTH], has_hi[DEPTH];
+#pragma unroll
+        for (int d = 0; d < DEPTH; ++d) {
+            // the nearest face (ties to the lowest axis), the chord, and the
+            // epoch coordinate at the chord midpoint: m_bar + w
+            const bool x0 = alive && ax[0].sn <= ax[1].sn && ax[0].sn <= ax[2].sn;
+            const bool x1 = alive && !x0 && ax[1].sn <= ax[2].sn;
+            const bool x2 = alive && !x0 && !x1;
+            const float s_exit = x0 ? ax[0].sn : (x1 ? ax[1].sn : ax[2].sn);
+            const float ds = s_exit - s_cur;
+            const float um = fmaf(L.mkk, s_cur + s_exit, L.c0);
+            const float fl = floorf(um);
+            const float w = um - fl;
+            const int mb = static_cast<int>(fl);
+            // -1 <= m_bar <= M - 1; snapshots m_bar (weight 1 - w) and m_bar + 1 (w)
+            const bool take = alive && ds > 0.f && static_cast<unsigned>(mb + 1) <= static_cast<unsigned>(M);
+            has_lo[d] = take && mb >= 0;
+            has_hi[d] = take && mb < M - 1 && w != 0.f;
+#ifdef GBD_CHECKED
+            if ((has_lo[d] && !check_cell(vol, err_word, kc[0], kc[1], kc[2], mb)) ||
+                (has_hi[d] && !check_cell(vol, err_word, kc[0], kc[1], kc[2], mb + 1)))
+                has_lo[d] = has_hi[d] = false;
+            kc[0] += x0 ? kd0 : 0;
+            kc[1] += x1 ? kd1 : 0;
+            kc[2] += x2 ? kd2 : 0;
+#endif
+            const int sum = ax[0].o + ax[1].o + ax[2].o;
+            // unpaired: snapshot m at block m; paired: snapshots mb and mb + 1
+            // side by side in block mb + 1
+            pa[d] = recb + static_cast<unsigned long long>(static_cast<long long>(PAIRED ? mb + 1 : mb) * es_bytes) +
+                    static_cast<unsigned long long>(static_cast<uint32_t>(sum)) * kUnit;
+            wgt[d] = take ? w : 0.f;
+            dsv[d] = take ? ds : 0.f;
+            step_lite<true>(ax, x0, x1, x2, ia0, ia1, ia2, tab);
+            s_cur = s_exit;
+            // past the last time that reaches a snapshot, or out of the box
+            alive = alive && s_exit <= L.s_stop && (ax[0].o | ax[1].o | ax[2].o) >= 0;
+        }
+        typename Rec::T rlo[DEPTH], rhi[DEPTH];
+#pragma unroll
+        for (int d = 0; d < DEPTH; ++d) {
+            rlo[d] = Rec::zero();
+            rhi[d] = Rec::zero();
+            if (PAIRED) {
+                if (has_lo[d] || has_hi[d]) Rec::load_pair_at(pa[d], rlo[d], rhi[d]);
+            } else {
+                if (has_lo[d]) rlo[d] = Rec::load_at(pa[d]);
+                if (has_hi[d]) rhi[d] = Rec::load_at(pa[d] + es_bytes);
+            }
+        }
+        // A snapshot a sample does not read is a zero record (boosted value
+        // exactly 0), and a sample not taken has weight and chord 0.
+#pragma unroll
+        for (int d = 0; d < DEPTH; ++d) {
+            const float2 vv = PLAIN ? Rec::boosted2_plain(rlo[d], rhi[d], bc) : Rec::boosted2(rlo[d], rhi[d], bc);
+            const float v = fmaf(wgt[d], vv.y - vv.x, vv.x);  // Eq. 8
+            acc = fmaf(v, dsv[d], acc);
+            count += (has_lo[d] || has_hi[d]) ? 1u : 0u;
+        }
+    }
+
+    if (in_image) {
+        const long long pix = static_cast<long long>(q) * width + p;
+        if (PARTIAL) {
+            if (count > 0u) atomicAdd(out_img + pix, acc);
+        } else if (accumulate) {
+            out_img[pix] += V.prefactor * acc;
+            if (cnt_img) cnt_img[pix] += count;
+        } else {
+            out_img[pix] = V.prefactor * acc;
+            if (cnt_img) cnt_img[pix] = count;
+        }
+    }
+}
+
+// step_lite with the exact epoch coordinate of each axis (float32 march).
+template <bool SMEM>
+__device__ __forceinline__ void step_nb(AxisState (&ax)[3], bool x0, bool x1, bool x2, float ia0, float ia1,
+                                        float ia2, long long du0, long long du1, long long du2, const int32_t *tab)
+{
+    step_lite<SMEM>(ax, x0, x1, x2, ia0, ia1, ia2, tab);
+    ax[0].un = x0 ? ax[0].un - du0 : ax[0].un;
+    ax[1].un = x1 ? ax[1].un - du1 : ax[1].un;
+    ax[2].un = x2 ? ax[2].un - du2 : ax[2].un;
+}
+
+// The march of march_ray for float32 records without branches: the step of
+// march_ray_bf16 (every lane executes it; a lane whose ray has ended takes no
+// step and reads no record) with the exact Q31.32 epoch coordinate, the
+// float32 Doppler factor of Eq. 14 and the compensated sum.  Its arithmetic
+// is that of the branching form, value for value.
+template <int DEPTH, bool PAIRED, bool PARTIAL>
+__device__ __forceinline__ void march_ray_f32(const VolDev &vol, const ViewDev &V, const RayBox &B, int p, int q,
+                                              int width, int height, float *out_img, uint32_t *cnt_img,
+                                              int *err_word, const int32_t *__restrict__ tab, bool accumulate)
+{
+    using Rec = Record<GBD_STORE_F32>;
+    const bool in_image = (p < width) && (q < height);
+    RayState R;
+    setup_ray<true>(R, vol, V, B, p, q, in_image, V.win_lo, V.win_hi, tab);
+    AxisState (&ax)[3] = R.ax;
+    bool alive = R.alive;
+    float s_cur = R.s_cur;
+    long long u_cur = R.u_cur;
+    const float ia0 = V.inv_a[0], ia1 = V.inv_a[1], ia2 = V.inv_a[2];
+    const long long du0 = V.du[0], du1 = V.du[1], du2 = V.du[2];
+    const int Mm1 = vol.M - 1;
+#ifdef GBD_CHECKED
+    int (&kc)[3] = R.kc;
+    const int kd0 = R.kd[0], kd1 = R.kd[1], kd2 = R.kd[2];
+#endif
+    BoostConsts bc;
+    bc.shx = V.sh_hi[0]; bc.shy = V.sh_hi[1]; bc.shz = V.sh_hi[2];
+    bc.slx = V.sh_lo[0]; bc.sly = V.sh_lo[1]; bc.slz = V.sh_lo[2];
+    bc.expo = V.expo;
+    bc.beaming = (V.flags & GBD_BEAMING) != 0u;
+    bc.plain = false;
+    // block b starts at byte recb + b es_bytes; a cell's record (paired: its
+    // record pair) is kUnit bytes at its layout offset.  Paired: a sample that
+    // reads no snapshot loads the zero record pair after the last block
+    // (faster for 32-byte pairs than a predicated load).
+    constexpr unsigned long long kUnit = PAIRED ? 32ull : 16ull;
+    const unsigned long long recb = reinterpret_cast<unsigned long long>(vol.rec);
+    const long long es_bytes = vol.epoch_stride * 16LL;
+    const unsigned long long zero_addr = recb + static_cast<unsigned long long>((vol.M + 1) * es_bytes);
+
+    float acc = 0.f, comp = 0.f;
+    uint32_t count = 0;
+    while (__any_sync(kFull, alive)) {
+        unsigned long long pa[DEPTH];
+        float wgt[DEPTH], dsv[DEPTH];
+        bool has_lo[DEPTH], has_hi[DEPTH];
+#pragma unroll
+        for (int d = 0; d < DEPTH; ++d) {
+            const bool x0 = alive && ax[0].sn <= ax[1].sn && ax[0].sn <= ax[2].sn;
+            const bool x1 = alive && !x0 && ax[1].sn <= ax[2].sn;
+            const bool x2 = alive && !x0 && !x1;
+            const float s_exit = x0 ? ax[0].sn : (x1 ? ax[1].sn : ax[2].sn);
+            const long long u_exit = x0 ? ax[0].un : (x1 ? ax[1].un : ax[2].un);
+            const float ds = s_exit - s_cur;
+            // epoch coordinate at the chord midpoint: m_bar + w, w in [0, 1)
+            const long long um = (u_cur + u_exit) >> 1;
+            const int mb = static_cast<int>(um >> 32);
+            const uint32_t frac = static_cast<uint32_t>(um);
+            const float w = static_cast<float>(frac) * 2.3283064365386963e-10f;
+            // -1 <= m_bar <= M - 1 (at u = -1 exactly both weights vanish)
+            const bool take = alive && ds > 0.f && static_cast<unsigned>(mb + 1) <= static_cast<unsigned>(Mm1 + 1);
+            has_lo[d] = take && mb >= 0;
+            has_hi[d] = take && mb < Mm1 && frac != 0u;
+#ifdef GBD_CHECKED
+            if ((has_lo[d] && !check_cell(vol, err_word, kc[0], kc[1], kc[2], mb)) ||
+                (has_hi[d] && !check_cell(vol, err_word, kc[0], kc[1], kc[2], mb + 1)))
+                has_lo[d] = has_hi[d] = false;
+            kc[0] += x0 ? kd0 : 0;
+            kc[1] += x1 ? kd1 : 0;
+            kc[2] += x2 ? kd2 : 0;
+#endif
+            const int sum = ax[0].o + ax[1].o + ax[2].o;
+            const unsigned long long a = recb + static_cast<unsigned long long>(static_cast<long long>(PAIRED ? mb + 1 : mb) * es_bytes) +
+                    static_cast<unsigned long long>(static_cast<uint32_t>(sum)) * kUnit;
+            pa[d] = PAIRED ? ((has_lo[d] || has_hi[d]) ? a : zero_addr) : a;
+            wgt[d] = w;
+            dsv[d] = ds;
+            step_nb<true>(ax, x0, x1, x2, ia0, ia1, ia2, du0, du1, du2, tab);
+            s_cur = s_exit;
+            u_cur = u_exit;
+            // past the last time that reaches a snapshot (u < -1), or out of the box
+            alive = alive && static_cast<int>(u_exit >> 32) >= -1 && (ax[0].o | ax[1].o | ax[2].o) >= 0;
+        }
+        typename Rec::T rlo[DEPTH], rhi[DEPTH];
+#pragma unroll
+        for (int d = 0; d < DEPTH; ++d) {
+            if (PAIRED) {
+                const float4 *ptr = reinterpret_cast<const float4 *>(pa[d]);
+                rlo[d] = __ldg(ptr);
+                rhi[d] = __ldg(ptr + 1);
+            } else {
+                rlo[d] = has_lo[d] ? __ldg(reinterpret_cast<const float4 *>(pa[d])) : Rec::zero();
+                rhi[d] = has_hi[d] ? __ldg(reinterpret_cast<const float4 *>(pa[d] + es_bytes)) : Rec::zero();
+            }
+        }
+#pragma unroll
+        for (int d = 0; d < DEPTH; ++d) {
+            // a snapshot the sample does not read is a zero record (boosted
+            // value exactly 0); the compensated sum takes the sample only where
+            // it read one
+            const float vlo = Rec::boosted(rlo[d], bc);
+            const float vhi = Rec::boosted(rhi[d], bc);
+            const float v = fmaf(wgt[d], vhi - vlo, vlo);  // Eq. 8
+            const float y = fmaf(v, dsv[d], -comp);
+            const float t = acc + y;
+            const bool take = has_lo[d] || has_hi[d];
+            comp = take ? (t - acc) - y : comp;
+            acc = take ? t : acc;
+            count += take ? 1u : 0u;
+        }
+    }
+    if (in_image) {
+        const long long pix = static_cast<long long>(q) * width + p;
+        if (PARTIAL) {
+            if (count > 0u) atomicAdd(out_img + pix, acc);
+        } else if (accumulate) {
+            out_img[pix] += V.prefactor * acc;
+            if (cnt_img) cnt_img[pix] += count;
+        } else {
+            out_img[pix] = V.prefactor * acc;
+            if (cnt_img) cnt_img[pix] = count;
+        }
+    }
+}
+
 // Marches the ray of pixel (p, q) of one image through box B.  Direct
 // (PARTIAL false): stores the pixel value (Eq. 19, with the prefactor) and,
 // if cnt_img is set, its cell-sample count, or adds them to what is there
@@ -472,6 +824,20 @@ __device__ __forceinline__ void march_ray(const VolDev &vol, const ViewDev &V, c
                                           const int32_t *__restrict__ tab, bool accumulate = false,
                                           const ChanPtrs ch = ChanPtrs{nullptr, 0, 0, nullptr})
 {
+    if constexpr (STORE == GBD_STORE_BF16_F16U && NCH == 0 && !TOUCH && SMEM) {
+        if (vol.plain_boost)
+            march_ray_bf16<DEPTH, PAIRED, PARTIAL, true>(vol, V, B, p, q, width, height, out_img, cnt_img, err_word,
+                                                         tab, accumulate);
+        else
+            march_ray_bf16<DEPTH, PAIRED, PARTIAL, false>(vol, V, B, p, q, width, height, out_img, cnt_img, err_word,
+                                                          tab, accumulate);
+        return;
+    }
+    if constexpr (STORE == GBD_STORE_F32 && NCH == 0 && !TOUCH && SMEM) {
+        march_ray_f32<DEPTH, PAIRED, PARTIAL>(vol, V, B, p, q, width, height, out_img, cnt_img, err_word, tab,
+                                              accumulate);
+        return;
+    }
     using Rec = Record<STORE>;
     const bool in_image = (p < width) && (q < height);
     RayState R;
@@ -680,6 +1046,241 @@ __device__ __forceinline__ void march_ray(const VolDev &vol, const ViewDev &V, c
     }
 }
 
+// march_group for bfloat16/float16 records, with the float epoch coordinate
+// of the bfloat16/float16 march (EpochLine of the reference member) and the
+// step without branches.  Member g's coordinate at a chord midpoint is the
+// reference member's plus dlf[g] = Delta_g rounded to float.
+template <bool PAIRED, int G, bool PLAIN>
+__device__ __forceinline__ void march_group_bf16(const VolDev &vol, const ViewDev &V, float win_lo, float win_hi,
+                                                 const ViewDev *GV, const long long *dl, const int *dh, int gcnt,
+                                                 const RayBox &B, int p, int q, int width, int height, float *out,
+                                                 long long img_stride, uint32_t *cnt_img, int *err_word,
+                                                 const int32_t *__restrict__ tab)
+{
+    using Rec = Record<GBD_STORE_BF16_F16U>;
+    const bool in_image = (p < width) && (q < height);
+    RayState R;
+    setup_ray<true>(R, vol, V, B, p, q, in_image, win_lo, win_hi, tab);
+    AxisState (&ax)[3] = R.ax;
+    bool alive = R.alive;
+    float s_cur = R.s_cur;
+    const float ia0 = V.inv_a[0], ia1 = V.inv_a[1], ia2 = V.inv_a[2];
+    const EpochLine L = epoch_line(R, V);
+    const int M = vol.M;
+#ifdef GBD_CHECKED
+    int (&kc)[3] = R.kc;
+    const int kd0 = R.kd[0], kd1 = R.kd[1], kd2 = R.kd[2];
+#endif
+
+    BoostConsts bc;
+    bc.shx = V.sh_hi[0]; bc.shy = V.sh_hi[1]; bc.shz = V.sh_hi[2];
+    bc.slx = V.sh_lo[0]; bc.sly = V.sh_lo[1]; bc.slz = V.sh_lo[2];
+    bc.expo = V.expo;
+    bc.beaming = (V.flags & GBD_BEAMING) != 0u;
+    bc.plain = PLAIN;
+    constexpr unsigned long long kUnit = PAIRED ? 16ull : 8ull;
+    const unsigned long long recb = reinterpret_cast<unsigned long long>(vol.rec);
+    const long long es_bytes = vol.epoch_stride * 8LL;
+
+    float dlf[G];
+    float acc[G];
+    uint32_t count[G];
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+        dlf[g] = g < gcnt ? fix_to_float(dl[g], 1.0f / kTwo32) : 0.f;
+        acc[g] = 0.f;
+        count[g] = 0u;
+    }
+
+    while (__any_sync(kFull, alive)) {
+        const bool x0 = alive && ax[0].sn <= ax[1].sn && ax[0].sn <= ax[2].sn;
+        const bool x1 = alive && !x0 && ax[1].sn <= ax[2].sn;
+        const bool x2 = alive && !x0 && !x1;
+        const float s_exit = x0 ? ax[0].sn : (x1 ? ax[1].sn : ax[2].sn);
+        const float ds = s_exit - s_cur;
+        const float um = fmaf(L.mkk, s_cur + s_exit, L.c0);  // the reference member's
+        const bool pos = alive && ds > 0.f;
+        const int sm = ax[0].o + ax[1].o + ax[2].o;
+        // the warp's range of reference snapshot indices
+        const int mref = static_cast<int>(floorf(um));
+        const int mlo = __reduce_min_sync(kFull, pos ? mref : INT_MAX);
+        const int mhi = __reduce_max_sync(kFull, pos ? mref : INT_MIN);
+#ifdef GBD_CHECKED
+        const int kc0 = kc[0], kc1 = kc[1], kc2 = kc[2];
+        kc[0] += x0 ? kd0 : 0;
+        kc[1] += x1 ? kd1 : 0;
+        kc[2] += x2 ? kd2 : 0;
+#endif
+        step_lite<true>(ax, x0, x1, x2, ia0, ia1, ia2, tab);
+        s_cur = s_exit;
+        alive = alive && s_exit <= L.s_stop && (ax[0].o | ax[1].o | ax[2].o) >= 0;
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+            // Member g's snapshot index at a midpoint is mref + dh[g] or one
+            // more: skip it when no lane of the warp can reach [-1, M - 1].
+            if (g >= gcnt || mlo > mhi || static_cast<long long>(mhi) + dh[g] < -2 ||
+                static_cast<long long>(mlo) + dh[g] > M - 1)
+                continue;
+            const float ug = um + dlf[g];
+            const float fl = floorf(ug);
+            const float w = ug - fl;
+            const int mb = static_cast<int>(fl);
+            const bool take = pos && static_cast<unsigned>(mb + 1) <= static_cast<unsigned>(M);
+            bool has_lo = take && mb >= 0;
+            bool has_hi = take && mb < M - 1 && w != 0.f;
+#ifdef GBD_CHECKED
+            if ((has_lo && !check_cell(vol, err_word, kc0, kc1, kc2, mb)) ||
+                (has_hi && !check_cell(vol, err_word, kc0, kc1, kc2, mb + 1)))
+                has_lo = has_hi = false;
+#endif
+            const unsigned long long pa =
+                recb + static_cast<unsigned long long>(static_cast<long long>(PAIRED ? mb + 1 : mb) * es_bytes) +
+                static_cast<unsigned long long>(static_cast<uint32_t>(sm)) * kUnit;
+            typename Rec::T rlo = Rec::zero(), rhi = Rec::zero();
+            if (PAIRED) {
+                if (has_lo || has_hi) Rec::load_pair_at(pa, rlo, rhi);
+            } else {
+                if (has_lo) rlo = Rec::load_at(pa);
+                if (has_hi) rhi = Rec::load_at(pa + es_bytes);
+            }
+            const float2 vv = PLAIN ? Rec::boosted2_plain(rlo, rhi, bc) : Rec::boosted2(rlo, rhi, bc);
+            const float v = fmaf(take ? w : 0.f, vv.y - vv.x, vv.x);  // Eq. 8
+            acc[g] = fmaf(v, take ? ds : 0.f, acc[g]);
+            count[g] += (has_lo || has_hi) ? 1u : 0u;
+        }
+    }
+
+    if (in_image) {
+        const long long pix = static_cast<long long>(q) * width + p;
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+            if (g >= gcnt) break;
+            out[g * img_stride + pix] = GV[g].prefactor * acc[g];
+            if (cnt_img) cnt_img[g * img_stride + pix] = count[g];
+        }
+    }
+}
+
+// march_group for float32 records without branches (the step of
+// march_ray_f32), exact epoch coordinate and compensated sums.  Each member's
+// arithmetic is that of the branching form, value for value.
+template <bool PAIRED, int G>
+__device__ __forceinline__ void march_group_f32(const VolDev &vol, const ViewDev &V, float win_lo, float win_hi,
+                                                const ViewDev *GV, const long long *dl, const int *dh, int gcnt,
+                                                const RayBox &B, int p, int q, int width, int height, float *out,
+                                                long long img_stride, uint32_t *cnt_img, int *err_word,
+                                                const int32_t *__restrict__ tab)
+{
+    using Rec = Record<GBD_STORE_F32>;
+    const bool in_image = (p < width) && (q < height);
+    RayState R;
+    setup_ray<true>(R, vol, V, B, p, q, in_image, win_lo, win_hi, tab);
+    AxisState (&ax)[3] = R.ax;
+    bool alive = R.alive;
+    float s_cur = R.s_cur;
+    long long u_cur = R.u_cur;
+    const float ia0 = V.inv_a[0], ia1 = V.inv_a[1], ia2 = V.inv_a[2];
+    const long long du0 = V.du[0], du1 = V.du[1], du2 = V.du[2];
+    const int Mm1 = vol.M - 1;
+#ifdef GBD_CHECKED
+    int (&kc)[3] = R.kc;
+    const int kd0 = R.kd[0], kd1 = R.kd[1], kd2 = R.kd[2];
+#endif
+    BoostConsts bc;
+    bc.shx = V.sh_hi[0]; bc.shy = V.sh_hi[1]; bc.shz = V.sh_hi[2];
+    bc.slx = V.sh_lo[0]; bc.sly = V.sh_lo[1]; bc.slz = V.sh_lo[2];
+    bc.expo = V.expo;
+    bc.beaming = (V.flags & GBD_BEAMING) != 0u;
+    bc.plain = false;
+    constexpr unsigned long long kUnit = PAIRED ? 32ull : 16ull;
+    const unsigned long long recb = reinterpret_cast<unsigned long long>(vol.rec);
+    const long long es_bytes = vol.epoch_stride * 16LL;
+    const unsigned long long zero_addr = recb + static_cast<unsigned long long>((vol.M + 1) * es_bytes);
+
+    float acc[G], comp[G];
+    uint32_t count[G];
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+        acc[g] = comp[g] = 0.f;
+        count[g] = 0u;
+    }
+
+    while (__any_sync(kFull, alive)) {
+        const bool x0 = alive && ax[0].sn <= ax[1].sn && ax[0].sn <= ax[2].sn;
+        const bool x1 = alive && !x0 && ax[1].sn <= ax[2].sn;
+        const bool x2 = alive && !x0 && !x1;
+        const float s_exit = x0 ? ax[0].sn : (x1 ? ax[1].sn : ax[2].sn);
+        const long long u_exit = x0 ? ax[0].un : (x1 ? ax[1].un : ax[2].un);
+        const float ds = s_exit - s_cur;
+        const long long um = (u_cur + u_exit) >> 1;  // reference epoch coordinate at the chord midpoint
+        const bool pos = alive && ds > 0.f;
+        const int sm = ax[0].o + ax[1].o + ax[2].o;
+        const int mref = static_cast<int>(um >> 32);
+        const int mlo = __reduce_min_sync(kFull, pos ? mref : INT_MAX);
+        const int mhi = __reduce_max_sync(kFull, pos ? mref : INT_MIN);
+#ifdef GBD_CHECKED
+        const int kc0 = kc[0], kc1 = kc[1], kc2 = kc[2];
+        kc[0] += x0 ? kd0 : 0;
+        kc[1] += x1 ? kd1 : 0;
+        kc[2] += x2 ? kd2 : 0;
+#endif
+        step_nb<true>(ax, x0, x1, x2, ia0, ia1, ia2, du0, du1, du2, tab);
+        s_cur = s_exit;
+        u_cur = u_exit;
+        alive = alive && static_cast<int>(u_exit >> 32) >= -1 && (ax[0].o | ax[1].o | ax[2].o) >= 0;
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+            // Member g's snapshot index at a midpoint is mref + dh[g] or one
+            // more: skip it when no lane of the warp can reach [-1, M - 1].
+            if (g >= gcnt || mlo > mhi || static_cast<long long>(mhi) + dh[g] < -2 ||
+                static_cast<long long>(mlo) + dh[g] > Mm1)
+                continue;
+            const long long ug = um + dl[g];
+            const int mb = static_cast<int>(ug >> 32);
+            const uint32_t frac = static_cast<uint32_t>(ug);
+            const float w = static_cast<float>(frac) * 2.3283064365386963e-10f;
+            const bool take = pos && static_cast<unsigned>(mb + 1) <= static_cast<unsigned>(Mm1 + 1);
+            bool has_lo = take && mb >= 0;
+            bool has_hi = take && mb < Mm1 && frac != 0u;
+#ifdef GBD_CHECKED
+            if ((has_lo && !check_cell(vol, err_word, kc0, kc1, kc2, mb)) ||
+                (has_hi && !check_cell(vol, err_word, kc0, kc1, kc2, mb + 1)))
+                has_lo = has_hi = false;
+#endif
+            const unsigned long long a =
+                recb + static_cast<unsigned long long>(static_cast<long long>(PAIRED ? mb + 1 : mb) * es_bytes) +
+                static_cast<unsigned long long>(static_cast<uint32_t>(sm)) * kUnit;
+            typename Rec::T rlo, rhi;
+            if (PAIRED) {
+                const float4 *ptr = reinterpret_cast<const float4 *>((has_lo || has_hi) ? a : zero_addr);
+                rlo = __ldg(ptr);
+                rhi = __ldg(ptr + 1);
+            } else {
+                rlo = has_lo ? __ldg(reinterpret_cast<const float4 *>(a)) : Rec::zero();
+                rhi = has_hi ? __ldg(reinterpret_cast<const float4 *>(a + es_bytes)) : Rec::zero();
+            }
+            const float vlo = Rec::boosted(rlo, bc), vhi = Rec::boosted(rhi, bc);
+            const float v = fmaf(w, vhi - vlo, vlo);     // Eq. 8
+            const float y = fmaf(v, ds, -comp[g]);       // compensated sum
+            const float t = acc[g] + y;
+            const bool tk = has_lo || has_hi;
+            comp[g] = tk ? (t - acc[g]) - y : comp[g];
+            acc[g] = tk ? t : acc[g];
+            count[g] += tk ? 1u : 0u;
+        }
+    }
+
+    if (in_image) {
+        const long long pix = static_cast<long long>(q) * width + p;
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+            if (g >= gcnt) break;
+            out[g * img_stride + pix] = GV[g].prefactor * acc[g];
+            if (cnt_img) cnt_img[g * img_stride + pix] = count[g];
+        }
+    }
+}
+
 // Time groups (batched renders).  Views that differ only in observer time
 // (and so in window and prefactor) share their rays; one lane marches its ray
 // once for up to kGroupMax such views.  The traversal covers the union of the
@@ -701,143 +1302,19 @@ __device__ __forceinline__ void march_group(const VolDev &vol, const ViewDev &V,
                                             long long img_stride, uint32_t *cnt_img, int *err_word,
                                             const int32_t *__restrict__ tab)
 {
-    using Rec = Record<STORE>;
-    const bool in_image = (p < width) && (q < height);
-    RayState R;
-    setup_ray<true>(R, vol, V, B, p, q, in_image, win_lo, win_hi, tab);
-    AxisState (&ax)[3] = R.ax;
-    bool &alive = R.alive;
-    float &s_cur = R.s_cur;
-    long long &u_cur = R.u_cur;
-    const float ia0 = V.inv_a[0], ia1 = V.inv_a[1], ia2 = V.inv_a[2];
-    const long long du0 = V.du[0], du1 = V.du[1], du2 = V.du[2];
-#ifdef GBD_CHECKED
-    int (&kc)[3] = R.kc;
-    const int kd0 = R.kd[0], kd1 = R.kd[1], kd2 = R.kd[2];
-#endif
-    const int Mm1 = vol.M - 1;
-
-    BoostConsts bc;
-    bc.shx = V.sh_hi[0]; bc.shy = V.sh_hi[1]; bc.shz = V.sh_hi[2];
-    bc.slx = V.sh_lo[0]; bc.sly = V.sh_lo[1]; bc.slz = V.sh_lo[2];
-    bc.expo = V.expo;
-    bc.beaming = (V.flags & GBD_BEAMING) != 0u;
-    const long long es = vol.epoch_stride;
-    const void *recs = vol.rec;
-
-    float acc[G], comp[G];
-    uint32_t count[G];
-#pragma unroll
-    for (int g = 0; g < G; ++g) {
-        acc[g] = comp[g] = 0.f;
-        count[g] = 0u;
+    if constexpr (STORE == GBD_STORE_F32) {
+        march_group_f32<PAIRED, G>(vol, V, win_lo, win_hi, GV, dl, dh, gcnt, B, p, q, width, height, out, img_stride,
+                                   cnt_img, err_word, tab);
+        return;
     }
-
-    while (__any_sync(kFull, alive)) {
-        long long um[DEPTH];  // reference epoch coordinate at the chord midpoint
-        float dsv[DEPTH];
-        int sm[DEPTH];        // layout offset of the cell
-        bool pos[DEPTH];      // a positive chord
-#ifdef GBD_CHECKED
-        int kcs[DEPTH][3];
-#endif
-        int mlo = INT_MAX, mhi = INT_MIN;  // the warp's range of reference snapshot indices
-#pragma unroll
-        for (int d = 0; d < DEPTH; ++d) {
-            um[d] = 0;
-            dsv[d] = 0.f;
-            sm[d] = 0;
-            pos[d] = false;
-            if (alive) {
-                const bool x0 = ax[0].sn <= ax[1].sn && ax[0].sn <= ax[2].sn;
-                const bool x1 = !x0 && ax[1].sn <= ax[2].sn;
-                const float s_exit = x0 ? ax[0].sn : (x1 ? ax[1].sn : ax[2].sn);
-                const long long u_exit = x0 ? ax[0].un : (x1 ? ax[1].un : ax[2].un);
-                const float ds = s_exit - s_cur;
-                um[d] = (u_cur + u_exit) >> 1;
-                pos[d] = ds > 0.f;
-                if (pos[d]) {
-                    const int mb = static_cast<int>(um[d] >> 32);
-                    mlo = min(mlo, mb);
-                    mhi = max(mhi, mb);
-                }
-                sm[d] = ax[0].o + ax[1].o + ax[2].o;
-                dsv[d] = ds;
-#ifdef GBD_CHECKED
-                kcs[d][0] = kc[0];
-                kcs[d][1] = kc[1];
-                kcs[d][2] = kc[2];
-#endif
-                step_exit<true>(ax, x0, x1, ia0, ia1, ia2, du0, du1, du2, tab);
-#ifdef GBD_CHECKED
-                kc[0] += x0 ? kd0 : 0;
-                kc[1] += x1 ? kd1 : 0;
-                kc[2] += (!x0 && !x1) ? kd2 : 0;
-#endif
-                s_cur = s_exit;
-                u_cur = u_exit;
-                alive = static_cast<int>(u_exit >> 32) >= -1 && (ax[0].o | ax[1].o | ax[2].o) >= 0;
-            }
-        }
-        mlo = __reduce_min_sync(kFull, mlo);
-        mhi = __reduce_max_sync(kFull, mhi);
-#pragma unroll
-        for (int g = 0; g < G; ++g) {
-            // Member g's snapshot index at a midpoint is mb + dh[g] or one
-            // more (dh = Delta_g rounded down to whole epochs): skip it when
-            // no lane of the warp can reach [-1, M - 1].
-            if (g >= gcnt || mlo > mhi || static_cast<long long>(mhi) + dh[g] < -2 ||
-                static_cast<long long>(mlo) + dh[g] > Mm1)
-                continue;
-            typename Rec::T rlo[DEPTH], rhi[DEPTH];
-            float wg[DEPTH];
-            bool take[DEPTH];
-#pragma unroll
-            for (int d = 0; d < DEPTH; ++d) {
-                const long long ug = um[d] + dl[g];
-                const int mb = static_cast<int>(ug >> 32);
-                const uint32_t frac = static_cast<uint32_t>(ug);
-                wg[d] = static_cast<float>(frac) * 2.3283064365386963e-10f;
-                const bool inside = pos[d] && static_cast<unsigned>(mb + 1) <= static_cast<unsigned>(Mm1 + 1);
-                bool has_lo = inside && mb >= 0;
-                bool has_hi = inside && (mb < Mm1) && (frac != 0u);
-#ifdef GBD_CHECKED
-                if ((has_lo && !check_cell(vol, err_word, kcs[d][0], kcs[d][1], kcs[d][2], mb)) ||
-                    (has_hi && !check_cell(vol, err_word, kcs[d][0], kcs[d][1], kcs[d][2], mb + 1)))
-                    has_lo = has_hi = false;
-#endif
-                take[d] = has_lo || has_hi;
-                rlo[d] = Rec::zero();
-                rhi[d] = Rec::zero();
-                if (PAIRED) {
-                    if (take[d]) Rec::load_pair(recs, static_cast<long long>(mb + 1) * es + 2LL * sm[d], rlo[d], rhi[d]);
-                } else {
-                    if (has_lo) rlo[d] = Rec::load(recs, static_cast<long long>(mb) * es + sm[d]);
-                    if (has_hi) rhi[d] = Rec::load(recs, static_cast<long long>(mb + 1) * es + sm[d]);
-                }
-            }
-#pragma unroll
-            for (int d = 0; d < DEPTH; ++d) {
-                const float2 vv = Rec::boosted2(rlo[d], rhi[d], bc);
-                const float vlo = vv.x, vhi = vv.y;
-                const float v = fmaf(wg[d], vhi - vlo, vlo);       // Eq. 8
-                const float y = fmaf(v, dsv[d], -comp[g]);         // compensated sum
-                const float t = acc[g] + y;
-                comp[g] = take[d] ? (t - acc[g]) - y : comp[g];
-                acc[g] = take[d] ? t : acc[g];
-                count[g] += take[d] ? 1u : 0u;
-            }
-        }
-    }
-
-    if (in_image) {
-        const long long pix = static_cast<long long>(q) * width + p;
-#pragma unroll
-        for (int g = 0; g < G; ++g) {
-            if (g >= gcnt) break;
-            out[g * img_stride + pix] = GV[g].prefactor * acc[g];
-            if (cnt_img) cnt_img[g * img_stride + pix] = count[g];
-        }
+    if constexpr (STORE == GBD_STORE_BF16_F16U) {
+        if (vol.plain_boost)
+            march_group_bf16<PAIRED, G, true>(vol, V, win_lo, win_hi, GV, dl, dh, gcnt, B, p, q, width, height, out,
+                                              img_stride, cnt_img, err_word, tab);
+        else
+            march_group_bf16<PAIRED, G, false>(vol, V, win_lo, win_hi, GV, dl, dh, gcnt, B, p, q, width, height, out,
+                                               img_stride, cnt_img, err_word, tab);
+        return;
     }
 }
 
@@ -856,7 +1333,7 @@ __global__ void __launch_bounds__(256, MINB) march_kernel(const __grid_constant_
 {
     extern __shared__ int32_t s_tab[];
     const int ntab = march_table_entries(a.vol.n);
-    for (int i = threadIdx.x; i < ntab; i += blockDim.x) s_tab[i] = a.vol.mtab[i];
+    stage_tables(s_tab, a.vol.mtab, ntab);
     __syncthreads();
 
     const int lane = threadIdx.x & 31;
@@ -938,7 +1415,7 @@ __global__ void __launch_bounds__(256, 3) group_kernel(const __grid_constant__ M
 {
     extern __shared__ int32_t s_tab[];
     const int ntab = march_table_entries(a.vol.n);
-    for (int i = threadIdx.x; i < ntab; i += blockDim.x) s_tab[i] = a.vol.mtab[i];
+    stage_tables(s_tab, a.vol.mtab, ntab);
     __syncthreads();
 
     const int lane = threadIdx.x & 31;
@@ -994,7 +1471,7 @@ __global__ void __launch_bounds__(256, MINB) vector_kernel(const __grid_constant
 {
     extern __shared__ int32_t s_tab[];
     const int ntab = march_table_entries(a.vol.n);
-    for (int i = threadIdx.x; i < ntab; i += blockDim.x) s_tab[i] = a.vol.mtab[i];
+    stage_tables(s_tab, a.vol.mtab, ntab);
     __syncthreads();
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
@@ -1043,7 +1520,7 @@ __global__ void __launch_bounds__(256, 1) touch_kernel(const __grid_constant__ M
 {
     extern __shared__ int32_t s_tab[];
     const int ntab = march_table_entries(a.vol.n);
-    for (int i = threadIdx.x; i < ntab; i += blockDim.x) s_tab[i] = a.vol.mtab[i];
+    stage_tables(s_tab, a.vol.mtab, ntab);
     __syncthreads();
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
@@ -1090,7 +1567,7 @@ __global__ void __launch_bounds__(256, MINB) wave_kernel(const __grid_constant__
     }
     const ReqDev &R = a.reqs[lo];
     const int ntab = march_table_entries(R.vol.n);
-    for (int i = threadIdx.x; i < ntab; i += blockDim.x) s_tab[i] = R.vol.mtab[i];
+    stage_tables(s_tab, R.vol.mtab, ntab);
     __syncthreads();
     const int tile = (b - R.cta_begin) * wpc + warp;
     if (tile >= R.tiles_x * R.tiles_y) return;
@@ -1168,6 +1645,7 @@ __global__ void __launch_bounds__(256, MINB) region_kernel(const __grid_constant
         for (int j = threadIdx.x; j < len + 2; j += blockDim.x)
             s_tab[i * (a.region + 2) + j] = j < len ? a.vol.mtab[src + j] : kTabSentinel;
     }
+    if (threadIdx.x < kTabPad) s_tab[3 * (a.region + 2) + threadIdx.x] = kTabSentinel;
     __syncthreads();
     // pixels whose centres project into the region's box, with a pixel of margin
     const int p_lo = max(static_cast<int>(floorf(pc - hp)) - 1, 0);
@@ -1319,7 +1797,7 @@ cudaError_t launch_wave(const WaveArgs &a, const LaunchCfg &cfg, cudaStream_t st
     // shared memory for the largest march tables of the launch
     int smem = 0;
     for (int r = 0; r < a.n_reqs; ++r)
-        smem = std::max(smem, static_cast<int>(sizeof(int32_t)) * march_table_entries(a.reqs[r].vol.n));
+        smem = std::max(smem, static_cast<int>(sizeof(int32_t)) * (march_table_entries(a.reqs[r].vol.n) + kTabPad));
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;
@@ -1380,7 +1858,7 @@ cudaError_t launch_region(const RegionArgs &a, const LaunchCfg &cfg, cudaStream_
     const long long regions = static_cast<long long>(a.nreg[0]) * a.nreg[1] * a.nreg[2];
     const int ctas = a.cta_begin[a.n_views];
     if (ctas < 1 || regions < 1 || regions > 65535) return cudaErrorInvalidValue;
-    const int smem = static_cast<int>(sizeof(int32_t)) * 3 * (a.region + 2);
+    const int smem = static_cast<int>(sizeof(int32_t)) * (3 * (a.region + 2) + kTabPad);
     void *params[] = {const_cast<RegionArgs *>(&a)};
     return cudaLaunchKernel(k, dim3(static_cast<unsigned>(ctas), static_cast<unsigned>(regions)),
                             dim3(32 * cfg.cta_warps), params, smem, stream);
@@ -1416,7 +1894,7 @@ cudaError_t plan_march(MarchArgs &a, const LaunchCfg &cfg, int num_sms, const do
         for (int v = v0; v < v1; ++v) uwork[u] += work ? std::max(work[v], 0.0) : 1.0;
     }
     const int threads = 32 * cfg.cta_warps;
-    const int smem = static_cast<int>(sizeof(int32_t)) * march_table_entries(a.vol.n);
+    const int smem = static_cast<int>(sizeof(int32_t)) * (march_table_entries(a.vol.n) + kTabPad);
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;

@@ -36,6 +36,7 @@ __global__ void pack_kernel(const PackArgs a)
     const int32_t *offx = a.axis_off;
     const int32_t *offy = a.axis_off + nx;
     const int32_t *offz = a.axis_off + nx + ny;
+    float g2max = 0.f;  // largest Gamma^2 of this thread's stored bfloat16/float16 records
     for (long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; i < ncell;
          i += static_cast<long long>(gridDim.x) * blockDim.x) {
         const int ix = static_cast<int>(i % nx);
@@ -74,10 +75,19 @@ __global__ void pack_kernel(const PackArgs a)
             rec.x = static_cast<uint32_t>(__bfloat16_as_ushort(jb)) | (static_cast<uint32_t>(__half_as_ushort(ux)) << 16);
             rec.y = static_cast<uint32_t>(__half_as_ushort(uy)) | (static_cast<uint32_t>(__half_as_ushort(uz)) << 16);
             if (!ok) rec = make_uint2(0u, 0u);
+            // Gamma^2 of the stored u, as the march computes it from the
+            // float16 values
+            const float fx = __half2float(ux), fy = __half2float(uy), fz = __half2float(uz);
+            if (ok) g2max = fmaxf(g2max, fmaf(fx, fx, fmaf(fy, fy, fmaf(fz, fz, 1.0f))));
             reinterpret_cast<uint2 *>(a.dst)[off] = rec;
             if (a.paired) reinterpret_cast<uint2 *>(a.dst)[off2] = rec;
         }
         if (!ok) atomicExch(a.bad, 1);
+    }
+    if (a.gamma2_max) {
+        // one atomic per warp (non-negative floats order as their bits)
+        for (int o = 16; o > 0; o >>= 1) g2max = fmaxf(g2max, __shfl_xor_sync(0xffffffffu, g2max, o));
+        if ((threadIdx.x & 31) == 0 && g2max > 0.f) atomicMax(a.gamma2_max, __float_as_uint(g2max));
     }
 }
 

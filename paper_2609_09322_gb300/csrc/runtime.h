@@ -22,6 +22,7 @@ struct Volume {
     int store = GBD_STORE_F32;
     int brick = 8, super_brick = 4;
     int paired = 0;                  // blocks of side-by-side snapshot pairs
+    int plain_boost = 0;             // bfloat16/float16 records with Gamma^2 <= kPlainGamma2
     int morton_cells = 0;            // Morton order of the cells inside a brick
     void *rec = nullptr;             // records, block after block
     int32_t *axis_off = nullptr;     // per-axis offset tables (n_x + n_y + n_z), then the march tables
