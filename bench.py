@@ -16,8 +16,9 @@ Workloads (synthetic, seeded; see gen/):
                render requests.
 
 Default run (no --workload): the suite.  The top-level line is the batched
-workload's batch render; nested entries (key "configs") carry the time-delay
-workload as float32 time groups and as bfloat16/float16 records, the
+workload's batch render; nested entries (key "configs") carry the batched
+workload stored as bfloat16/float16 records, the time-delay workload in
+float32 (lone march, and time groups) and as bfloat16/float16 records, the
 precision workload in bfloat16/float16, the plain float32 per-image march of
 each workload (one render call per view, default layout and launch), and a
 short serving phase with p50/p99 latency.  Each entry has its own roofline
@@ -65,9 +66,11 @@ RECORD_BYTES = {"f32": 16, "bf16": 8}
 # [, region edge [, time-group size]]) and layout (brick, super-brick, paired)
 # that the autotuner picks for each workload on GB300.
 PINNED = {
-    "batched": ("4,8,4,2,1,64", "8,4,1"),
-    "time_delay": ("4,8,4,2,1,0,4", "4,2,1"),
-    "time_delay_bf16": ("4,8,4,4,1,0,1", "4,2,1"),
+    "batched": ("4,8,4,2,1,64", "4,4,0"),
+    "batched_bf16": ("4,8,4,2,1,128", "4,4,0"),
+    "time_delay": ("4,8,4,2,1,0,1", "4,4,0"),
+    "time_delay_grouped": ("4,8,4,2,1,0,4", "4,2,1"),
+    "time_delay_bf16": ("8,4,8,4,1,0,1", "4,2,1"),
     "precision": ("4,8,4,4,1,0,2", "8,4,1"),
 }
 L2_NOTE = "inputs larger than L2 (resident volume %.1f GB; L2 129 MB), no flush between steps"
@@ -382,13 +385,20 @@ def run_suite(args, rank: int, world: int):
             top["config"]["tuned"] = {k: tuned[k] for k in ("ms", "candidates")}
         batched_images = images
         ctx.unload(vol)
-        # the plain per-image march of the same workload (default layout and launch)
-        vol, info, _ = load_volume(ctx, wl, "f32", (0, 0, 0))
-        e, img, _ = march_entry(ctx, wl, vol, info, None, stream, max(3, min(args.steps, 5)), 3, world, dev,
-                                per_image=True, clk=clk)
-        e.pop("_t")
-        nested["batched_f32_per_image"] = with_oracle_error(e, wl, img, oracle_s)
-        ctx.unload(vol)
+        # the same workload stored as bfloat16/float16 records, and the plain
+        # float32 per-image march (default layout and launch)
+        for key, store, form in (("batched_bf16", "bf16", "batched_bf16"), ("batched_f32_per_image", "f32", None)):
+            launch = parse_launch(PINNED[form][0]) if form else None
+            layout = parse_layout(PINNED[form][1]) if form else (0, 0, 0)
+            vol, info, _ = load_volume(ctx, wl, store, layout)
+            e, img, _ = march_entry(ctx, wl, vol, info, launch, stream, args.steps if form else max(3, min(args.steps, 5)),
+                                    args.warmup if form else 3, world, dev, per_image=form is None, clk=clk)
+            e.pop("_t")
+            if form:
+                e["roofline"]["traffic"] = recorded_traffic(form, launch, layout)
+                e["config"]["workload"] += "; stored as bf16 j' + fp16 u"
+            nested[key] = with_oracle_error(e, wl, img, oracle_s)
+            ctx.unload(vol)
         torch.cuda.empty_cache()
         cpu = None
         if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -402,7 +412,8 @@ def run_suite(args, rank: int, world: int):
 
         # ---- time-delay: float32 time groups, bfloat16/float16 records, per-image
         wl = make_workload("time_delay", args.scale)
-        for key, store, form in (("time_delay_f32_grouped", "f32", "time_delay"),
+        for key, store, form in (("time_delay_f32", "f32", "time_delay"),
+                                 ("time_delay_f32_grouped", "f32", "time_delay_grouped"),
                                  ("time_delay_bf16", "bf16", "time_delay_bf16"),
                                  ("time_delay_f32_per_image", "f32", None)):
             launch = parse_launch(PINNED[form][0]) if form else None
@@ -633,7 +644,7 @@ def run_gpu(args, rank: int, world: int):
     bytes_per_sample = rec * (2 if wl["lookback"] else 1) + extra_bytes_per_sample
     compulsory = ctx.touched_records(vol, views) * rec if args.form == "batch" else None
     kernel_ms = statistics.median(per_step)
-    tag = args.workload if not (args.workload == "time_delay" and wl["store"] == "bf16") else "time_delay_bf16"
+    tag = args.workload + ("_bf16" if args.store == "bf16" and args.workload != "precision" else "")
     traffic = (recorded_traffic(tag, launch, parse_layout(args.layout))
                if args.form == "batch" and not args.per_image else None)
     value = world * samples_per_step / (ms_per_step * 1e-3) / 1e9
@@ -928,7 +939,7 @@ def main():
         result = run_suite(args, rank, world)
     else:
         if args.workload in PINNED and not args.launch and not args.tune and not args.per_image:
-            key = "time_delay_bf16" if args.workload == "time_delay" and args.store == "bf16" else args.workload
+            key = args.workload + ("_bf16" if args.store == "bf16" and args.workload != "precision" else "")
             args.launch = PINNED[key][0]
             args.layout = args.layout or PINNED[key][1]
         result, wl = run_gpu(args, rank, world)

@@ -513,6 +513,11 @@ RegionProj region_proj(const ViewDev &V)
     }
     P.p0 = static_cast<float>(p0);
     P.q0 = static_cast<float>(q0);
+    for (int i = 0; i < 3; ++i) {
+        P.g0f[i] = static_cast<float>(g0[i]);
+        P.guf[i] = static_cast<float>(m[i][0]);
+        P.gvf[i] = static_cast<float>(m[i][1]);
+    }
     return P;
 }
 

@@ -146,6 +146,9 @@ constexpr int kViewsPerRegionLaunch = 96;
 struct RegionProj {
     float ip[3], iq[3];
     float p0, q0;
+    // and back: pixel (p, q) lies on its ray near g0f + p guf + q gvf (float
+    // approximations of the view's fixed-point g0, gu, gv)
+    float g0f[3], guf[3], gvf[3];
 };
 
 struct RegionArgs {

@@ -1595,10 +1595,13 @@ __global__ void __launch_bounds__(256, MINB) wave_kernel(const __grid_constant__
 
 // Region schedule (RegionArgs): CTA (x, y) marches rays of one view through
 // region y.  The region's table terms along each axis (forward or reversed,
-// as the view needs), followed by two sentinels, are staged in shared memory;
-// the view's pixels whose rays can cross the region are those inside the
-// projection of the region's box, and the CTA's warps take packets of that
-// rectangle.  Each ray adds its region sum to its partial slot.
+// as the view needs), followed by two sentinels, are staged in shared memory.
+// The view's pixels whose rays can cross the region lie in the projection of
+// the region's box; the CTA takes one packet of that rectangle per warp,
+// keeps the rays that cross the box, sorts them by the length of their chord
+// through it (8 buckets, longest first) and hands them to its warps 32 at a
+// time, so that the rays of a warp end at about the same step.  Each ray adds
+// its region sum to its partial slot.
 template <int STORE, int DEPTH, int MINB, bool PAIRED>
 __global__ void __launch_bounds__(256, MINB) region_kernel(const __grid_constant__ RegionArgs a)
 {
@@ -1652,18 +1655,70 @@ __global__ void __launch_bounds__(256, MINB) region_kernel(const __grid_constant
     const int p_hi = min(static_cast<int>(floorf(pc + hp)) + 1, a.width - 1);
     const int q_lo = max(static_cast<int>(floorf(qc - hq)) - 1, 0);
     const int q_hi = min(static_cast<int>(floorf(qc + hq)) + 1, a.height - 1);
-    if (p_hi < p_lo || q_hi < q_lo) return;
     const int tx0 = p_lo / a.packet_w, ty0 = q_lo / a.packet_h;
     const int ntx = p_hi / a.packet_w - tx0 + 1;
     const int nty = q_hi / a.packet_h - ty0 + 1;
-    const int tile = cb * wpc + warp;
-    if (tile >= ntx * nty) return;
-    const int p = (tx0 + tile % ntx) * a.packet_w + lane % a.packet_w;
-    const int q = (ty0 + tile / ntx) * a.packet_h + lane / a.packet_w;
+    // Screen the CTA's packets (one per warp): does the pixel's ray cross the
+    // region's box inside the window, and how long is its chord there?  The
+    // float slab test runs against the box grown by 0.01 cells, far above its
+    // rounding (the exact set-up of the march still decides), so no ray the
+    // march would sample is dropped.  The chord is bounded by the crossing
+    // time of any one axis, which scales the 8 buckets.
+    __shared__ int s_cnt[8][8];
+    __shared__ uint32_t s_pix[256];
+    int p = a.width, q = a.height, bucket = 8;
+    {
+        const int tile = cb * wpc + warp;
+        const int ntiles = (p_hi < p_lo || q_hi < q_lo) ? 0 : ntx * nty;
+        const int nx1 = max(ntx, 1);
+        const int pp = (tx0 + tile % nx1) * a.packet_w + lane % a.packet_w;
+        const int qq = (ty0 + tile / nx1) * a.packet_h + lane / a.packet_w;
+        bool hit = tile < ntiles && pp < a.width && qq < a.height;
+        float s_lo = V.win_lo, s_hi = V.win_hi, smax = 3.0e38f;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            const float g = fmaf(static_cast<float>(qq), P.gvf[i], fmaf(static_cast<float>(pp), P.guf[i], P.g0f[i]));
+            const float lo = static_cast<float>(B.lo[i]) - 0.01f, hi = static_cast<float>(B.hi[i]) + 0.01f;
+            if (V.inv_a[i] != 0.f) {
+                s_lo = fmaxf(s_lo, (lo - g) * V.inv_a[i]);
+                s_hi = fminf(s_hi, (hi - g) * V.inv_a[i]);
+                smax = fminf(smax, (hi - lo) * V.inv_a[i]);
+            } else {
+                hit = hit && g >= lo && g < hi;
+            }
+        }
+        hit = hit && s_hi > s_lo - 1e-3f * (1.f + fabsf(s_lo));
+        if (hit) {
+            bucket = 7 - min(7, max(0, static_cast<int>((s_hi - s_lo) / smax * 8.0f)));
+            p = pp;
+            q = qq;
+        }
+    }
+    for (int k = 0; k < 8; ++k) {
+        const uint32_t m = __ballot_sync(kFull, bucket == k);
+        if (lane == 0) s_cnt[k][warp] = __popc(m);
+    }
+    __syncthreads();
+    int pos = 0, total = 0;
+    for (int k = 0; k < 8; ++k)
+        for (int w = 0; w < wpc; ++w) {
+            const int c = s_cnt[k][w];
+            pos += (k < bucket || (k == bucket && w < warp)) ? c : 0;
+            total += c;
+        }
+    {
+        const uint32_t m = __match_any_sync(kFull, bucket);
+        pos += __popc(m & ((1u << lane) - 1u));
+    }
+    if (bucket < 8) s_pix[pos] = static_cast<uint32_t>(p) | (static_cast<uint32_t>(q) << 16);
+    __syncthreads();
+    const int k = warp * 32 + lane;
+    const uint32_t pq = k < total ? s_pix[k] : (static_cast<uint32_t>(a.width) | (static_cast<uint32_t>(a.height) << 16));
+    if (__all_sync(kFull, k >= total)) return;
     float *out = a.partial + static_cast<long long>(slot) * a.slot_stride +
                  static_cast<long long>(a.batch_view[vi]) * a.width * a.height;
-    march_ray<STORE, DEPTH, PAIRED, true, true>(a.vol, V, B, p, q, a.width, a.height, out, nullptr, a.error_word,
-                                                s_tab);
+    march_ray<STORE, DEPTH, PAIRED, true, true>(a.vol, V, B, static_cast<int>(pq & 0xffffu), static_cast<int>(pq >> 16),
+                                                a.width, a.height, out, nullptr, a.error_word, s_tab);
 }
 
 // out = prefactor * (partial slots summed in slot order, compensated).
