@@ -1649,7 +1649,8 @@ __global__ void __launch_bounds__(256, MINB) region_kernel(const __grid_constant
             s_tab[i * (a.region + 2) + j] = j < len ? a.vol.mtab[src + j] : kTabSentinel;
     }
     if (threadIdx.x < kTabPad) s_tab[3 * (a.region + 2) + threadIdx.x] = kTabSentinel;
-    __syncthreads();
+    // (the barrier after the screening below also covers the staged tables,
+    // so their loads overlap the screening arithmetic)
     // pixels whose centres project into the region's box, with a pixel of margin
     const int p_lo = max(static_cast<int>(floorf(pc - hp)) - 1, 0);
     const int p_hi = min(static_cast<int>(floorf(pc + hp)) + 1, a.width - 1);
@@ -1698,7 +1699,7 @@ __global__ void __launch_bounds__(256, MINB) region_kernel(const __grid_constant
         const uint32_t m = __ballot_sync(kFull, bucket == k);
         if (lane == 0) s_cnt[k][warp] = __popc(m);
     }
-    __syncthreads();
+    __syncthreads();  // tables staged, bucket counts written
     int pos = 0, total = 0;
     for (int k = 0; k < 8; ++k)
         for (int w = 0; w < wpc; ++w) {
