@@ -70,7 +70,7 @@ PINNED = {
     "batched_bf16": ("4,8,4,2,1,128", "4,4,0"),
     "time_delay": ("4,8,4,2,1,0,1", "4,4,0"),
     "time_delay_grouped": ("4,8,4,2,1,0,4", "4,2,1"),
-    "time_delay_bf16": ("8,4,8,4,1,0,1", "4,2,1"),
+    "time_delay_bf16": ("8,4,8,4,1,0,4", "4,2,1"),
     "precision": ("4,8,4,4,1,0,2", "8,4,1"),
 }
 L2_NOTE = "inputs larger than L2 (resident volume %.1f GB; L2 129 MB), no flush between steps"

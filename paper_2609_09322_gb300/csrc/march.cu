@@ -1049,8 +1049,10 @@ __device__ __forceinline__ void march_ray(const VolDev &vol, const ViewDev &V, c
 // march_group for bfloat16/float16 records, with the float epoch coordinate
 // of the bfloat16/float16 march (EpochLine of the reference member) and the
 // step without branches.  Member g's coordinate at a chord midpoint is the
-// reference member's plus dlf[g] = Delta_g rounded to float.
-template <bool PAIRED, int G, bool PLAIN>
+// reference member's plus dlf[g] = Delta_g rounded to float.  GD cells are
+// traversed per iteration; then each member gathers its records of all GD
+// cells before evaluating them, so a member keeps GD loads in flight.
+template <bool PAIRED, int G, bool PLAIN, int GD>
 __device__ __forceinline__ void march_group_bf16(const VolDev &vol, const ViewDev &V, float win_lo, float win_hi,
                                                  const ViewDev *GV, const long long *dl, const int *dh, int gcnt,
                                                  const RayBox &B, int p, int q, int width, int height, float *out,
@@ -1093,27 +1095,40 @@ __device__ __forceinline__ void march_group_bf16(const VolDev &vol, const ViewDe
     }
 
     while (__any_sync(kFull, alive)) {
-        const bool x0 = alive && ax[0].sn <= ax[1].sn && ax[0].sn <= ax[2].sn;
-        const bool x1 = alive && !x0 && ax[1].sn <= ax[2].sn;
-        const bool x2 = alive && !x0 && !x1;
-        const float s_exit = x0 ? ax[0].sn : (x1 ? ax[1].sn : ax[2].sn);
-        const float ds = s_exit - s_cur;
-        const float um = fmaf(L.mkk, s_cur + s_exit, L.c0);  // the reference member's
-        const bool pos = alive && ds > 0.f;
-        const int sm = ax[0].o + ax[1].o + ax[2].o;
-        // the warp's range of reference snapshot indices
-        const int mref = static_cast<int>(floorf(um));
-        const int mlo = __reduce_min_sync(kFull, pos ? mref : INT_MAX);
-        const int mhi = __reduce_max_sync(kFull, pos ? mref : INT_MIN);
+        float umv[GD], dsv[GD];  // reference member's epoch coordinate at the chord midpoints, chords
+        int smv[GD];             // layout offsets of the cells
+        bool posv[GD];           // positive chords
 #ifdef GBD_CHECKED
-        const int kc0 = kc[0], kc1 = kc[1], kc2 = kc[2];
-        kc[0] += x0 ? kd0 : 0;
-        kc[1] += x1 ? kd1 : 0;
-        kc[2] += x2 ? kd2 : 0;
+        int kcs[GD][3];
 #endif
-        step_lite<true>(ax, x0, x1, x2, ia0, ia1, ia2, tab);
-        s_cur = s_exit;
-        alive = alive && s_exit <= L.s_stop && (ax[0].o | ax[1].o | ax[2].o) >= 0;
+        int mlo = INT_MAX, mhi = INT_MIN;  // the warp's range of reference snapshot indices
+#pragma unroll
+        for (int d = 0; d < GD; ++d) {
+            const bool x0 = alive && ax[0].sn <= ax[1].sn && ax[0].sn <= ax[2].sn;
+            const bool x1 = alive && !x0 && ax[1].sn <= ax[2].sn;
+            const bool x2 = alive && !x0 && !x1;
+            const float s_exit = x0 ? ax[0].sn : (x1 ? ax[1].sn : ax[2].sn);
+            dsv[d] = s_exit - s_cur;
+            umv[d] = fmaf(L.mkk, s_cur + s_exit, L.c0);
+            posv[d] = alive && dsv[d] > 0.f;
+            smv[d] = ax[0].o + ax[1].o + ax[2].o;
+            const int mref = static_cast<int>(floorf(umv[d]));
+            mlo = posv[d] ? min(mlo, mref) : mlo;
+            mhi = posv[d] ? max(mhi, mref) : mhi;
+#ifdef GBD_CHECKED
+            kcs[d][0] = kc[0];
+            kcs[d][1] = kc[1];
+            kcs[d][2] = kc[2];
+            kc[0] += x0 ? kd0 : 0;
+            kc[1] += x1 ? kd1 : 0;
+            kc[2] += x2 ? kd2 : 0;
+#endif
+            step_lite<true>(ax, x0, x1, x2, ia0, ia1, ia2, tab);
+            s_cur = s_exit;
+            alive = alive && s_exit <= L.s_stop && (ax[0].o | ax[1].o | ax[2].o) >= 0;
+        }
+        mlo = __reduce_min_sync(kFull, mlo);
+        mhi = __reduce_max_sync(kFull, mhi);
 #pragma unroll
         for (int g = 0; g < G; ++g) {
             // Member g's snapshot index at a midpoint is mref + dh[g] or one
@@ -1121,32 +1136,44 @@ __device__ __forceinline__ void march_group_bf16(const VolDev &vol, const ViewDe
             if (g >= gcnt || mlo > mhi || static_cast<long long>(mhi) + dh[g] < -2 ||
                 static_cast<long long>(mlo) + dh[g] > M - 1)
                 continue;
-            const float ug = um + dlf[g];
-            const float fl = floorf(ug);
-            const float w = ug - fl;
-            const int mb = static_cast<int>(fl);
-            const bool take = pos && static_cast<unsigned>(mb + 1) <= static_cast<unsigned>(M);
-            bool has_lo = take && mb >= 0;
-            bool has_hi = take && mb < M - 1 && w != 0.f;
+            typename Rec::T rlo[GD], rhi[GD];
+            float wg[GD];
+            bool tk[GD];
+#pragma unroll
+            for (int d = 0; d < GD; ++d) {
+                const float ug = umv[d] + dlf[g];
+                const float fl = floorf(ug);
+                const float w = ug - fl;
+                const int mb = static_cast<int>(fl);
+                const bool take = posv[d] && static_cast<unsigned>(mb + 1) <= static_cast<unsigned>(M);
+                bool has_lo = take && mb >= 0;
+                bool has_hi = take && mb < M - 1 && w != 0.f;
 #ifdef GBD_CHECKED
-            if ((has_lo && !check_cell(vol, err_word, kc0, kc1, kc2, mb)) ||
-                (has_hi && !check_cell(vol, err_word, kc0, kc1, kc2, mb + 1)))
-                has_lo = has_hi = false;
+                if ((has_lo && !check_cell(vol, err_word, kcs[d][0], kcs[d][1], kcs[d][2], mb)) ||
+                    (has_hi && !check_cell(vol, err_word, kcs[d][0], kcs[d][1], kcs[d][2], mb + 1)))
+                    has_lo = has_hi = false;
 #endif
-            const unsigned long long pa =
-                recb + static_cast<unsigned long long>(static_cast<long long>(PAIRED ? mb + 1 : mb) * es_bytes) +
-                static_cast<unsigned long long>(static_cast<uint32_t>(sm)) * kUnit;
-            typename Rec::T rlo = Rec::zero(), rhi = Rec::zero();
-            if (PAIRED) {
-                if (has_lo || has_hi) Rec::load_pair_at(pa, rlo, rhi);
-            } else {
-                if (has_lo) rlo = Rec::load_at(pa);
-                if (has_hi) rhi = Rec::load_at(pa + es_bytes);
+                const unsigned long long pa =
+                    recb + static_cast<unsigned long long>(static_cast<long long>(PAIRED ? mb + 1 : mb) * es_bytes) +
+                    static_cast<unsigned long long>(static_cast<uint32_t>(smv[d])) * kUnit;
+                rlo[d] = Rec::zero();
+                rhi[d] = Rec::zero();
+                if (PAIRED) {
+                    if (has_lo || has_hi) Rec::load_pair_at(pa, rlo[d], rhi[d]);
+                } else {
+                    if (has_lo) rlo[d] = Rec::load_at(pa);
+                    if (has_hi) rhi[d] = Rec::load_at(pa + es_bytes);
+                }
+                wg[d] = take ? w : 0.f;
+                tk[d] = has_lo || has_hi;
             }
-            const float2 vv = PLAIN ? Rec::boosted2_plain(rlo, rhi, bc) : Rec::boosted2(rlo, rhi, bc);
-            const float v = fmaf(take ? w : 0.f, vv.y - vv.x, vv.x);  // Eq. 8
-            acc[g] = fmaf(v, take ? ds : 0.f, acc[g]);
-            count[g] += (has_lo || has_hi) ? 1u : 0u;
+#pragma unroll
+            for (int d = 0; d < GD; ++d) {
+                const float2 vv = PLAIN ? Rec::boosted2_plain(rlo[d], rhi[d], bc) : Rec::boosted2(rlo[d], rhi[d], bc);
+                const float v = fmaf(wg[d], vv.y - vv.x, vv.x);  // Eq. 8
+                acc[g] = fmaf(v, posv[d] ? dsv[d] : 0.f, acc[g]);
+                count[g] += tk[d] ? 1u : 0u;
+            }
         }
     }
 
@@ -1309,11 +1336,11 @@ __device__ __forceinline__ void march_group(const VolDev &vol, const ViewDev &V,
     }
     if constexpr (STORE == GBD_STORE_BF16_F16U) {
         if (vol.plain_boost)
-            march_group_bf16<PAIRED, G, true>(vol, V, win_lo, win_hi, GV, dl, dh, gcnt, B, p, q, width, height, out,
-                                              img_stride, cnt_img, err_word, tab);
+            march_group_bf16<PAIRED, G, true, DEPTH>(vol, V, win_lo, win_hi, GV, dl, dh, gcnt, B, p, q, width, height,
+                                                     out, img_stride, cnt_img, err_word, tab);
         else
-            march_group_bf16<PAIRED, G, false>(vol, V, win_lo, win_hi, GV, dl, dh, gcnt, B, p, q, width, height, out,
-                                               img_stride, cnt_img, err_word, tab);
+            march_group_bf16<PAIRED, G, false, DEPTH>(vol, V, win_lo, win_hi, GV, dl, dh, gcnt, B, p, q, width, height,
+                                                      out, img_stride, cnt_img, err_word, tab);
         return;
     }
 }
@@ -1407,7 +1434,8 @@ __global__ void __launch_bounds__(256, MINB) march_kernel(const __grid_constant_
 // Time groups: march_kernel's work split over groups of views instead of
 // single views (group g is views group_first[g] .. group_first[g + 1] - 1,
 // its CTAs cta_begin[g] .. cta_begin[g + 1] - 1, its tile counter queue[g]).
-// One cell per step (the members' gathers are the independent loads) and at
+// DEPTH cells per iteration for bfloat16/float16 records (each member
+// gathers all of them before evaluating any), one for float32 records, and at
 // most 80 registers: with the compiler's budget (110 - 150) fewer warps fit
 // and the grouped march ran slower than the lone one.
 template <int STORE, int DEPTH, bool PAIRED, int G>
@@ -1763,22 +1791,40 @@ void *select_cap(int depth, int capped, bool steal)
     return capped ? select_depth<STORE, 3, PAIRED>(depth, steal) : select_depth<STORE, 1, PAIRED>(depth, steal);
 }
 
-template <int STORE, bool PAIRED>
-void *select_group_size(int size)
+template <int STORE, bool PAIRED, int DEPTH>
+void *select_group_depth(int size)
 {
-    if (size == 4) return reinterpret_cast<void *>(&group_kernel<STORE, 1, PAIRED, 4>);
-    if (size == kGroupMax) return reinterpret_cast<void *>(&group_kernel<STORE, 1, PAIRED, kGroupMax>);
+    if (size == 4) return reinterpret_cast<void *>(&group_kernel<STORE, DEPTH, PAIRED, 4>);
+    if (size == kGroupMax) return reinterpret_cast<void *>(&group_kernel<STORE, DEPTH, PAIRED, kGroupMax>);
     return nullptr;
 }
 
+template <int STORE, bool PAIRED>
+void *select_group_size(int size, int depth)
+{
+    // float32 groups march one cell per iteration whatever the depth: with two
+    // or four, the extra record registers cost more warps than the loads gain
+    if constexpr (STORE == GBD_STORE_F32) {
+        return (depth == 1 || depth == 2 || depth == 4) ? select_group_depth<STORE, PAIRED, 1>(size) : nullptr;
+    } else {
+        switch (depth) {
+        case 1: return select_group_depth<STORE, PAIRED, 1>(size);
+        case 2: return select_group_depth<STORE, PAIRED, 2>(size);
+        case 4: return select_group_depth<STORE, PAIRED, 4>(size);
+        default: return nullptr;
+        }
+    }
+}
+
 // Time groups: a kernel for groups of up to 4 views and one for up to 8.
-void *select_group(int store, int paired, int size)
+void *select_group(int store, int paired, int size, int depth)
 {
     if (store == GBD_STORE_F32)
-        return paired ? select_group_size<GBD_STORE_F32, true>(size) : select_group_size<GBD_STORE_F32, false>(size);
+        return paired ? select_group_size<GBD_STORE_F32, true>(size, depth)
+                      : select_group_size<GBD_STORE_F32, false>(size, depth);
     if (store == GBD_STORE_BF16_F16U)
-        return paired ? select_group_size<GBD_STORE_BF16_F16U, true>(size)
-                      : select_group_size<GBD_STORE_BF16_F16U, false>(size);
+        return paired ? select_group_size<GBD_STORE_BF16_F16U, true>(size, depth)
+                      : select_group_size<GBD_STORE_BF16_F16U, false>(size, depth);
     return nullptr;
 }
 
@@ -1934,7 +1980,7 @@ cudaError_t plan_march(MarchArgs &a, const LaunchCfg &cfg, int num_sms, const do
 {
     // n_groups > 0: time groups, one unit of CTAs per group; else one per view
     const bool grouped = a.n_groups > 0;
-    void *k = grouped ? select_group(a.vol.store, a.vol.paired, a.group_size)
+    void *k = grouped ? select_group(a.vol.store, a.vol.paired, a.group_size, cfg.depth)
                       : select_kernel(a.vol.store, cfg.depth, cfg.regcap, a.vol.paired,
                                       a.persistent && a.n_views > 1);
     if (!k || a.n_views < 1 || a.n_views > kViewsPerLaunch) return cudaErrorInvalidValue;
