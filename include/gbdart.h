@@ -462,9 +462,11 @@ int gbd_relayout(gbd_ctx *ctx, gbd_volume vol, int32_t brick, int32_t super_bric
 
 /* Bounds checking.  In the library built with GBD_CHECKED every gather tests
  * its cell and epoch index against the volume; a violation skips the load and
- * sets a device word instead of faulting.  This call waits for the device,
- * stores that word in *out (0 = no violation; always 0 in the production
- * build) and clears it. */
+ * sets bit 0 of a device word instead of faulting.  In every build, the
+ * region schedule sets bit 1 if a region's ray list ever ran out of room (its
+ * size comes from a bound on the pixels a region can cover, so this does not
+ * happen; the rays past the end would go unmarched).  This call waits for the
+ * device, stores that word in *out (0 = no violation) and clears it. */
 int gbd_bounds_violations(gbd_ctx *ctx, int32_t *out);
 
 #ifdef __cplusplus

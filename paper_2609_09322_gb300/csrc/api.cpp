@@ -537,18 +537,27 @@ int region_slots(const Volume &vol, const LaunchCfg &cfg, const gbd_image_spec &
     return slots - 2;
 }
 
-// CTAs one view needs per region: the projection of a region's box covers at
-// most this many packets (a pixel of margin on each side, plus alignment).
+// CTAs one view needs per region: room for every pixel whose ray can cross a
+// region's box.  The box (edges grown by a cell, far above the screening
+// test's own margin and rounding) projects onto the image plane as the
+// zonotope spanned by its edge vectors f_i (pixels per cell along axis i
+// times the edge), of area A = sum_{i<j} |f_i x f_j| and half-perimeter
+// sum_i |f_i|; a convex set holds at most A + P / 2 + 1 points of a unit
+// lattice (Nosarzewska's bound), here the pixel centres.
 static int region_ctas(const RegionProj &P, int region, const LaunchCfg &cfg)
 {
-    double hp = 0.0, hq = 0.0;
+    const double edge = static_cast<double>(region) + 1.0;
+    double f[3][2], area = 0.0, half_perim = 0.0;
     for (int i = 0; i < 3; ++i) {
-        hp += std::fabs(static_cast<double>(P.ip[i])) * 0.5 * region;
-        hq += std::fabs(static_cast<double>(P.iq[i])) * 0.5 * region;
+        f[i][0] = static_cast<double>(P.ip[i]) * edge;
+        f[i][1] = static_cast<double>(P.iq[i]) * edge;
+        half_perim += std::hypot(f[i][0], f[i][1]);
     }
-    const long long ntx = static_cast<long long>((2.0 * hp + 5.0) / cfg.packet_w) + 2;
-    const long long nty = static_cast<long long>((2.0 * hq + 5.0) / cfg.packet_h) + 2;
-    return static_cast<int>((ntx * nty + cfg.cta_warps - 1) / cfg.cta_warps);
+    for (int i = 0; i < 3; ++i)
+        for (int j = i + 1; j < 3; ++j) area += std::fabs(f[i][0] * f[j][1] - f[i][1] * f[j][0]);
+    const double pixels = area + half_perim + 1.0;
+    const int per_cta = 32 * cfg.cta_warps;
+    return static_cast<int>(std::min(std::ceil(pixels / per_cta), 2.0e9 / per_cta));
 }
 
 // Order in which the region schedule launches a batch's views: by the Morton
@@ -573,18 +582,44 @@ static std::vector<int> direction_order(const std::vector<ViewDev> &hv)
     return order;
 }
 
-// Enqueues a region-schedule batch on st: clear the partial slots, march the
-// regions (one launch per kViewsPerRegionLaunch views in direction order, each
-// over all regions), then add up the slots into dev_out.  partial holds
-// slots * n * W * H floats.
+// Scratch of a region-schedule batch of the views hv: the partial slots
+// (slots * n * W * H floats), then the ray lists and their counts, which each
+// launch of the batch reuses in turn (room for the launch with the most CTAs:
+// at most kViewsPerRegionLaunch views of the most CTAs per region).
+size_t region_scratch_bytes(const Volume &vol, const LaunchCfg &cfg, const gbd_image_spec &spec,
+                            const std::vector<ViewDev> &hv, size_t *rays_off, size_t *count_off)
+{
+    int nreg[3];
+    const int slots = region_slots(vol, cfg, spec, nreg);
+    if (slots <= 0) return 0;
+    const size_t n = hv.size();
+    const size_t regions = static_cast<size_t>(nreg[0]) * nreg[1] * nreg[2];
+    size_t per_view = 0;
+    for (const ViewDev &V : hv) per_view = std::max(per_view, static_cast<size_t>(region_ctas(region_proj(V), cfg.region, cfg)));
+    const size_t views = std::min(n, static_cast<size_t>(kViewsPerRegionLaunch));
+    const size_t pbytes = (sizeof(float) * static_cast<size_t>(spec.width) * spec.height * n * slots + 255) / 256 * 256;
+    const size_t rbytes = (sizeof(uint32_t) * regions * views * per_view * 32 * cfg.cta_warps + 255) / 256 * 256;
+    const size_t cbytes = (sizeof(int) * regions * views + 255) / 256 * 256;
+    if (rays_off) *rays_off = pbytes;
+    if (count_off) *count_off = pbytes + rbytes;
+    return pbytes + rbytes + cbytes;
+}
+
+// Enqueues a region-schedule batch on st: clear the partial slots; per
+// kViewsPerRegionLaunch views in direction order, list each region's crossing
+// rays by chord length and march them (two launches over all regions); then
+// add up the slots into dev_out.  scratch holds region_scratch_bytes.
 cudaError_t enqueue_regions(Ctx &ctx, const Volume &vol, const std::vector<ViewDev> &hv, const gbd_image_spec &spec,
-                            const LaunchCfg &cfg, float *dev_out, float *partial, cudaStream_t st, int *launches)
+                            const LaunchCfg &cfg, float *dev_out, char *scratch, cudaStream_t st, int *launches)
 {
     int nreg[3];
     const int slots = region_slots(vol, cfg, spec, nreg);
     const int n = static_cast<int>(hv.size());
     const long long pix = static_cast<long long>(spec.width) * spec.height;
     const long long slot_stride = pix * n;
+    size_t rays_off = 0, count_off = 0;
+    region_scratch_bytes(vol, cfg, spec, hv, &rays_off, &count_off);
+    float *partial = reinterpret_cast<float *>(scratch);
     cudaError_t e = cudaMemsetAsync(partial, 0, sizeof(float) * static_cast<size_t>(slot_stride) * slots, st);
     auto a = std::make_unique<RegionArgs>();
     const std::vector<int> order = direction_order(hv);
@@ -603,6 +638,9 @@ cudaError_t enqueue_regions(Ctx &ctx, const Volume &vol, const std::vector<ViewD
         a->partial = partial;
         a->slot_stride = slot_stride;
         a->error_word = ctx.err_word;
+        a->rays = reinterpret_cast<uint32_t *>(scratch + rays_off);
+        a->ray_count = reinterpret_cast<int *>(scratch + count_off);
+        a->rays_per_cta = 32 * cfg.cta_warps;
         long long total = 0;
         for (int v = 0; v < cnt; ++v) {
             a->batch_view[v] = order[first + v];
@@ -613,8 +651,9 @@ cudaError_t enqueue_regions(Ctx &ctx, const Volume &vol, const std::vector<ViewD
         }
         if (total > 0x7fffffffLL) return cudaErrorInvalidValue;
         a->cta_begin[cnt] = static_cast<int>(total);
-        e = launch_region(*a, cfg, st);
-        ++*launches;
+        e = launch_screen(*a, st);
+        if (e == cudaSuccess) e = launch_region(*a, cfg, st);
+        *launches += 2;
     }
     auto r = std::make_unique<ReduceArgs>();
     for (int first = 0; first < n && e == cudaSuccess; first += kViewsPerRegionLaunch) {
@@ -645,14 +684,15 @@ int render_direct(Ctx &ctx, const Volume &vol, const std::vector<ViewDev> &hv, c
     int nreg[3];
     const int slots = region_slots(vol, cfg, spec, nreg);
     if (slots > 0) {
-        const size_t pbytes = sizeof(float) * pix * static_cast<size_t>(slots);
+        const size_t pbytes = region_scratch_bytes(vol, cfg, spec, hv, nullptr, nullptr);
         const size_t total = pbytes + (spec.out_on_host ? pix * sizeof(float) : 0);
         cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&scratch), total, st);
         if (e != cudaSuccess) return cuda_fail(e, "region scratch");
-        float *partial = reinterpret_cast<float *>(scratch);
         float *dev_out = spec.out_on_host ? reinterpret_cast<float *>(scratch + pbytes) : spec.out;
         int launches = 0;
-        e = enqueue_regions(ctx, vol, hv, spec, cfg, dev_out, partial, st, &launches);
+        e = cudaStreamWaitEvent(st, ctx.region_done, 0);
+        if (e == cudaSuccess) e = enqueue_regions(ctx, vol, hv, spec, cfg, dev_out, scratch, st, &launches);
+        if (e == cudaSuccess) e = cudaEventRecord(ctx.region_done, st);
         if (e == cudaSuccess && spec.out_on_host)
             e = cudaMemcpyAsync(spec.out, dev_out, pix * sizeof(float), cudaMemcpyDeviceToHost, st);
         cudaError_t ef = cudaFreeAsync(scratch, st);
@@ -705,7 +745,9 @@ struct GraphKey {
 // A batch graph: a memset of the tile counters, one kernel node per chunk of
 // views (independent, so they may run side by side), and, for host output,
 // the copy back.  New views of the same geometry update the kernel nodes'
-// parameters in place.
+// parameters in place.  A region-schedule batch is captured from
+// enqueue_regions instead (rebuilt for new views), and its copy back to host
+// memory is issued after each replay, outside the graph.
 struct GraphEntry {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -714,6 +756,7 @@ struct GraphEntry {
     std::vector<void *> kfuncs;  // the kernel of each node
     std::vector<ViewDev> views;  // the views the kernel nodes hold
     char *d_scratch = nullptr;   // tile counters (+ image when out_on_host)
+    float *region_img = nullptr; // region schedule with host output: the device image, copied back after each replay
     cudaEvent_t done = nullptr;
     bool launched = false;
     ~GraphEntry()
@@ -800,20 +843,18 @@ static int build_region_graph(Ctx &ctx, const Volume &vol, const GraphKey &key, 
                               const std::vector<ViewDev> &hv, int slots, GraphEntry &g)
 {
     const size_t pix = static_cast<size_t>(spec.width) * spec.height * key.n;
-    const size_t pbytes = sizeof(float) * pix * static_cast<size_t>(slots);
+    const size_t pbytes = region_scratch_bytes(vol, key.cfg, spec, hv, nullptr, nullptr);
     const size_t total = pbytes + (spec.out_on_host ? pix * sizeof(float) : 0);
     cudaError_t e = cudaMalloc(reinterpret_cast<void **>(&g.d_scratch), total);
     if (e != cudaSuccess) return cuda_fail(e, "region batch scratch");
     e = cudaEventCreateWithFlags(&g.done, cudaEventDisableTiming);
     if (e != cudaSuccess) return cuda_fail(e, "batch event");
-    float *partial = reinterpret_cast<float *>(g.d_scratch);
     float *dev_out = spec.out_on_host ? reinterpret_cast<float *>(g.d_scratch + pbytes) : spec.out;
+    if (spec.out_on_host) g.region_img = dev_out;
     cudaStream_t cap = ctx.capture_stream;
     e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return cuda_fail(e, "begin capture");
-    cudaError_t e2 = enqueue_regions(ctx, vol, hv, spec, key.cfg, dev_out, partial, cap, &g.region_launches);
-    if (e2 == cudaSuccess && spec.out_on_host)
-        e2 = cudaMemcpyAsync(spec.out, dev_out, pix * sizeof(float), cudaMemcpyDeviceToHost, cap);
+    cudaError_t e2 = enqueue_regions(ctx, vol, hv, spec, key.cfg, dev_out, g.d_scratch, cap, &g.region_launches);
     e = cudaStreamEndCapture(cap, &g.graph);
     if (e2 != cudaSuccess) return cuda_fail(e2, "capture region batch");
     if (e != cudaSuccess) return cuda_fail(e, "end capture");
@@ -937,7 +978,21 @@ int render_graph(Ctx &ctx, const Volume &vol, gbd_volume vid, const std::vector<
         }
         slot->views = hv;
     }
-    cudaError_t e = cudaGraphLaunch(slot->exec, st);
+    cudaError_t e = cudaSuccess;
+    if (slot->region_launches > 0) {
+        // one region batch marches at a time; host output is copied back
+        // outside the graph, after the march, so that it overlaps the next
+        // batch's march
+        e = cudaStreamWaitEvent(st, ctx.region_done, 0);
+        if (e == cudaSuccess) e = cudaGraphLaunch(slot->exec, st);
+        if (e == cudaSuccess) e = cudaEventRecord(ctx.region_done, st);
+        if (e == cudaSuccess && slot->region_img)
+            e = cudaMemcpyAsync(spec.out, slot->region_img,
+                                sizeof(float) * static_cast<size_t>(spec.width) * spec.height * hv.size(),
+                                cudaMemcpyDeviceToHost, st);
+    } else {
+        e = cudaGraphLaunch(slot->exec, st);
+    }
     if (e != cudaSuccess) return cuda_fail(e, "graph launch");
     e = cudaEventRecord(slot->done, st);
     if (e != cudaSuccess) return cuda_fail(e, "graph event");
@@ -1020,6 +1075,8 @@ int gbd_create(gbd_ctx **out, int32_t device, uint64_t hbm_budget_bytes)
     if (e != cudaSuccess) return cuda_fail(e, "error word");
     e = cudaMemset(ctx->err_word, 0, 256);
     if (e != cudaSuccess) return cuda_fail(e, "error word clear");
+    e = cudaEventCreateWithFlags(&ctx->region_done, cudaEventDisableTiming);
+    if (e != cudaSuccess) return cuda_fail(e, "region event");
     load_tune_file(*ctx);
     *out = ctx.release();
     return GBD_OK;
@@ -1041,6 +1098,7 @@ int gbd_destroy(gbd_ctx *ctx)
         }
         ctx->volumes.clear();
         if (ctx->err_word) cudaFree(ctx->err_word);
+        if (ctx->region_done) cudaEventDestroy(ctx->region_done);
         for (auto &kv : ctx->tile_orders) cudaFree(kv.second);
         ctx->tile_orders.clear();
         if (ctx->load_stream) cudaStreamDestroy(ctx->load_stream);

@@ -161,6 +161,14 @@ struct RegionArgs {
     float *partial;           // slot s of batch view b at partial + s * slot_stride + b * width * height
     long long slot_stride;    // floats per slot
     int *error_word;
+    // Ray lists (written by screen_kernel, read by region_kernel): the pixels
+    // (p | q << 16) of view v whose rays cross region r, longest chord first,
+    // at rays + (r * cta_begin[n_views] + cta_begin[v]) * rays_per_cta, and
+    // their number at ray_count[r * n_views + v].  Each list has room for all
+    // of the view's CTAs' rays in one region.
+    uint32_t *rays;
+    int *ray_count;
+    int rays_per_cta;         // 32 * warps per CTA of region_kernel
     int cta_begin[kViewsPerRegionLaunch + 1];  // CTAs of each view in one region (blockIdx.x)
     int batch_view[kViewsPerRegionLaunch];     // the view's index in the batch
     RegionProj proj[kViewsPerRegionLaunch];
@@ -233,7 +241,10 @@ cudaError_t launch_touch(MarchArgs &a, uint32_t *bits, long long cells, const La
 cudaError_t launch_vector(MarchArgs &a, int n_chan, const LaunchCfg &cfg, int num_sms, const double *work,
                           cudaStream_t stream);
 // Region schedule: the caller has filled everything but the grid, which
-// launch_region derives from cta_begin and the region counts.
+// launch_screen (one CTA per view and region) and launch_region derive from
+// cta_begin and the region counts.  launch_screen writes the ray lists that
+// the following launch_region of the same arguments marches.
+cudaError_t launch_screen(const RegionArgs &a, cudaStream_t stream);
 cudaError_t launch_region(const RegionArgs &a, const LaunchCfg &cfg, cudaStream_t stream);
 cudaError_t launch_reduce(const ReduceArgs &a, cudaStream_t stream);
 

@@ -1630,27 +1630,24 @@ __global__ void __launch_bounds__(256, MINB) wave_kernel(const __grid_constant__
 // through it (8 buckets, longest first) and hands them to its warps 32 at a
 // time, so that the rays of a warp end at about the same step.  Each ray adds
 // its region sum to its partial slot.
-template <int STORE, int DEPTH, int MINB, bool PAIRED>
-__global__ void __launch_bounds__(256, MINB) region_kernel(const __grid_constant__ RegionArgs a)
+// Region r of view vi: its box in the view's march frame (mirrored axes
+// mirrored) with the offsets of its staged march tables, its partial slot, and
+// the pixels p_lo .. p_lo + pw - 1, q_lo .. q_lo + qh - 1 of the image that
+// hold every pixel whose centre projects into the box, with a pixel of margin
+// (pw = qh = 0 if none).
+struct RegionFrame {
+    RayBox B;
+    int slot;
+    int p_lo, q_lo, pw, qh;
+};
+
+__device__ __forceinline__ RegionFrame region_frame(const RegionArgs &a, int vi, int r)
 {
-    extern __shared__ int32_t s_tab[];
-    const int lane = threadIdx.x & 31;
-    const int warp = threadIdx.x >> 5;
-    const int wpc = blockDim.x >> 5;
-    const int b = static_cast<int>(blockIdx.x);
-    int vi = 0, hi = a.n_views - 1;  // last view whose first CTA is <= b
-    while (vi < hi) {
-        const int mid = (vi + hi + 1) >> 1;
-        if (a.cta_begin[mid] <= b) vi = mid;
-        else hi = mid - 1;
-    }
-    const int cb = b - a.cta_begin[vi];
     const ViewDev &V = a.views[vi];
     const RegionProj &P = a.proj[vi];
-    const int r = static_cast<int>(blockIdx.y);
     const int rr[3] = {r % a.nreg[0], (r / a.nreg[0]) % a.nreg[1], r / (a.nreg[0] * a.nreg[1])};
-    RayBox B;
-    int slot = 0;
+    RegionFrame F;
+    F.slot = 0;
     float pc = P.p0, qc = P.q0, hp = 0.f, hq = 0.f;
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
@@ -1658,95 +1655,208 @@ __global__ void __launch_bounds__(256, MINB) region_kernel(const __grid_constant
         const int olo = rr[i] * a.region;
         const int ohi = min(olo + a.region, n);
         const bool mirrored = (V.flags & (kFlagMirror0 << i)) != 0u;
-        B.lo[i] = mirrored ? n - ohi : olo;
-        B.hi[i] = mirrored ? n - olo : ohi;
-        B.cur0[i] = 4u * static_cast<uint32_t>(i * (a.region + 2));
-        slot += mirrored ? a.nreg[i] - 1 - rr[i] : rr[i];
-        const float c = 0.5f * static_cast<float>(B.lo[i] + B.hi[i]);
-        const float h = 0.5f * static_cast<float>(B.hi[i] - B.lo[i]);
+        F.B.lo[i] = mirrored ? n - ohi : olo;
+        F.B.hi[i] = mirrored ? n - olo : ohi;
+        F.B.cur0[i] = 4u * static_cast<uint32_t>(i * (a.region + 2));
+        F.slot += mirrored ? a.nreg[i] - 1 - rr[i] : rr[i];
+        const float c = 0.5f * static_cast<float>(F.B.lo[i] + F.B.hi[i]);
+        const float h = 0.5f * static_cast<float>(F.B.hi[i] - F.B.lo[i]);
         pc = fmaf(P.ip[i], c, pc);
         qc = fmaf(P.iq[i], c, qc);
         hp = fmaf(fabsf(P.ip[i]), h, hp);
         hq = fmaf(fabsf(P.iq[i]), h, hq);
     }
-    for (int i = 0; i < 3; ++i) {
-        const bool mirrored = (V.flags & (kFlagMirror0 << i)) != 0u;
-        const int len = B.hi[i] - B.lo[i];
-        const int src = march_table_base(a.vol.n, i) + (mirrored ? a.vol.n[i] + 2 : 0) + B.lo[i];
-        for (int j = threadIdx.x; j < len + 2; j += blockDim.x)
-            s_tab[i * (a.region + 2) + j] = j < len ? a.vol.mtab[src + j] : kTabSentinel;
-    }
-    if (threadIdx.x < kTabPad) s_tab[3 * (a.region + 2) + threadIdx.x] = kTabSentinel;
-    // (the barrier after the screening below also covers the staged tables,
-    // so their loads overlap the screening arithmetic)
-    // pixels whose centres project into the region's box, with a pixel of margin
     const int p_lo = max(static_cast<int>(floorf(pc - hp)) - 1, 0);
     const int p_hi = min(static_cast<int>(floorf(pc + hp)) + 1, a.width - 1);
     const int q_lo = max(static_cast<int>(floorf(qc - hq)) - 1, 0);
     const int q_hi = min(static_cast<int>(floorf(qc + hq)) + 1, a.height - 1);
-    const int tx0 = p_lo / a.packet_w, ty0 = q_lo / a.packet_h;
-    const int ntx = p_hi / a.packet_w - tx0 + 1;
-    const int nty = q_hi / a.packet_h - ty0 + 1;
-    // Screen the CTA's packets (one per warp): does the pixel's ray cross the
-    // region's box inside the window, and how long is its chord there?  The
-    // float slab test runs against the box grown by 0.01 cells, far above its
-    // rounding (the exact set-up of the march still decides), so no ray the
-    // march would sample is dropped.  The chord is bounded by the crossing
-    // time of any one axis, which scales the 8 buckets.
-    __shared__ int s_cnt[8][8];
-    __shared__ uint32_t s_pix[256];
-    int p = a.width, q = a.height, bucket = 8;
-    {
-        const int tile = cb * wpc + warp;
-        const int ntiles = (p_hi < p_lo || q_hi < q_lo) ? 0 : ntx * nty;
-        const int nx1 = max(ntx, 1);
-        const int pp = (tx0 + tile % nx1) * a.packet_w + lane % a.packet_w;
-        const int qq = (ty0 + tile / nx1) * a.packet_h + lane / a.packet_w;
-        bool hit = tile < ntiles && pp < a.width && qq < a.height;
-        float s_lo = V.win_lo, s_hi = V.win_hi, smax = 3.0e38f;
+    const bool any = p_hi >= p_lo && q_hi >= q_lo;
+    F.p_lo = p_lo;
+    F.q_lo = q_lo;
+    F.pw = any ? p_hi - p_lo + 1 : 0;
+    F.qh = any ? q_hi - q_lo + 1 : 0;
+    return F;
+}
+
+// Chord classes of the ray lists: class 0 holds the longest chords.
+constexpr int kChordClasses = 64;
+// Warps per CTA of screen_kernel, and the candidates a warp classifies per
+// pass (a byte each in shared memory).
+constexpr int kScreenWarps = 8;
+constexpr int kScreenBatch = 2048;
+
+// Ray lists of the region schedule, one warp per view and region (view
+// fastest): the pixels of the region's projected bounding box whose rays
+// cross its box inside the view's window, in a counting sort by chord
+// length, so that each warp of region_kernel gets 32 rays of nearly equal
+// length.  The float slab test runs against the box grown by 0.01 cells, far
+// above its rounding (the exact set-up of the march still decides), so no ray
+// that the march would sample is dropped.  No chord in the box is longer than
+// the crossing time smax of any one axis, which scales the classes.
+// Candidates (the bounding box in row-major order) are taken kScreenBatch at a
+// time: classified and counted, then placed; each batch appends its own
+// sorted run.  The 32 candidates of a step lie along a row, where the chord
+// length changes smoothly: each run of lanes with one class takes its places
+// with one shared atomic.  The list has room for every pixel the box can cover (the
+// host's bound); were it ever full, the pixels past its end would be dropped
+// and bit 1 of the error word set.
+__global__ void __launch_bounds__(32 * kScreenWarps) screen_kernel(const __grid_constant__ RegionArgs a)
+{
+    __shared__ int s_off_all[kScreenWarps][kChordClasses];
+    __shared__ uint8_t s_cls_all[kScreenWarps][kScreenBatch];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int regions = a.nreg[0] * a.nreg[1] * a.nreg[2];
+    const long long pair = static_cast<long long>(blockIdx.x) * kScreenWarps + warp;
+    if (pair >= static_cast<long long>(a.n_views) * regions) return;
+    const int vi = static_cast<int>(pair % a.n_views), r = static_cast<int>(pair / a.n_views);
+    int *s_off = s_off_all[warp];
+    uint8_t *s_cls = s_cls_all[warp];
+    const ViewDev &V = a.views[vi];
+    const RegionProj &P = a.proj[vi];
+    const RegionFrame F = region_frame(a, vi, r);
+    const int cap = (a.cta_begin[vi + 1] - a.cta_begin[vi]) * a.rays_per_cta;
+    const int n_pix = F.pw * F.qh;
+    const int nc = (n_pix + 31) & ~31;  // the whole warp takes each step
+    const float inv_pw = F.pw > 0 ? 1.0f / static_cast<float>(F.pw) : 0.f;
+    float lo[3], hi[3], ia[3], g0[3], gu[3], gv[3];
+    float smax = 3.0e38f;
 #pragma unroll
-        for (int i = 0; i < 3; ++i) {
-            const float g = fmaf(static_cast<float>(qq), P.gvf[i], fmaf(static_cast<float>(pp), P.guf[i], P.g0f[i]));
-            const float lo = static_cast<float>(B.lo[i]) - 0.01f, hi = static_cast<float>(B.hi[i]) + 0.01f;
-            if (V.inv_a[i] != 0.f) {
-                s_lo = fmaxf(s_lo, (lo - g) * V.inv_a[i]);
-                s_hi = fminf(s_hi, (hi - g) * V.inv_a[i]);
-                smax = fminf(smax, (hi - lo) * V.inv_a[i]);
-            } else {
-                hit = hit && g >= lo && g < hi;
+    for (int k = 0; k < 3; ++k) {
+        lo[k] = static_cast<float>(F.B.lo[k]) - 0.01f;
+        hi[k] = static_cast<float>(F.B.hi[k]) + 0.01f;
+        ia[k] = V.inv_a[k];
+        g0[k] = P.g0f[k];
+        gu[k] = P.guf[k];
+        gv[k] = P.gvf[k];
+        if (ia[k] != 0.f) smax = fminf(smax, (hi[k] - lo[k]) * ia[k]);
+    }
+    const float cls_scale = static_cast<float>(kChordClasses) / smax;
+    const float win_lo = V.win_lo, win_hi = V.win_hi;
+    uint32_t *list = a.rays + (static_cast<long long>(r) * a.cta_begin[a.n_views] + a.cta_begin[vi]) * a.rays_per_cta;
+    const uint32_t below = (1u << lane) - 1u;
+    int done = 0;
+    for (int base = 0; base < nc; base += kScreenBatch) {
+        const int nb = min(nc - base, kScreenBatch);
+        s_off[lane] = 0;
+        s_off[lane + 32] = 0;
+        __syncwarp();
+        // classify and count (one leader lane per class updates its count)
+        for (int i = lane; i < nb; i += 32) {
+            const int j = base + i;  // row-major index in the bounding box
+            int qo = static_cast<int>(static_cast<float>(j) * inv_pw);
+            int po = j - qo * F.pw;
+            if (po < 0) { po += F.pw; --qo; }
+            if (po >= F.pw) { po -= F.pw; ++qo; }
+            const float p = static_cast<float>(F.p_lo + po), q = static_cast<float>(F.q_lo + qo);
+            bool hit = j < n_pix;
+            float s_lo = win_lo, s_hi = win_hi;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                const float g = fmaf(q, gv[k], fmaf(p, gu[k], g0[k]));
+                if (ia[k] != 0.f) {
+                    s_lo = fmaxf(s_lo, (lo[k] - g) * ia[k]);
+                    s_hi = fminf(s_hi, (hi[k] - g) * ia[k]);
+                } else {
+                    hit = hit && g >= lo[k] && g < hi[k];
+                }
+            }
+            hit = hit && s_hi > s_lo - 1e-3f * (1.f + fabsf(s_lo));
+            const float f = fminf(fmaxf((s_hi - s_lo) * cls_scale, 0.f), static_cast<float>(kChordClasses - 1));
+            const int c = hit ? kChordClasses - 1 - static_cast<int>(f) : kChordClasses;
+            s_cls[i] = static_cast<uint8_t>(c);
+            const int c_prev = __shfl_up_sync(kFull, c, 1);  // every lane takes part
+            const bool head = lane == 0 || c != c_prev;
+            const uint32_t heads = __ballot_sync(kFull, head);
+            if (head && c < kChordClasses) {
+                const uint32_t after = heads & ~below & ~(1u << lane);
+                atomicAdd(&s_off[c], (after ? __ffs(after) - 1 : 32) - lane);
             }
         }
-        hit = hit && s_hi > s_lo - 1e-3f * (1.f + fabsf(s_lo));
-        if (hit) {
-            bucket = 7 - min(7, max(0, static_cast<int>((s_hi - s_lo) / smax * 8.0f)));
-            p = pp;
-            q = qq;
+        __syncwarp();
+        // exclusive prefix sum over the classes, two per lane
+        const int c0 = s_off[2 * lane], c1 = s_off[2 * lane + 1];
+        int incl = c0 + c1;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int v = __shfl_up_sync(kFull, incl, d);
+            incl += lane >= d ? v : 0;
         }
-    }
-    for (int k = 0; k < 8; ++k) {
-        const uint32_t m = __ballot_sync(kFull, bucket == k);
-        if (lane == 0) s_cnt[k][warp] = __popc(m);
-    }
-    __syncthreads();  // tables staged, bucket counts written
-    int pos = 0, total = 0;
-    for (int k = 0; k < 8; ++k)
-        for (int w = 0; w < wpc; ++w) {
-            const int c = s_cnt[k][w];
-            pos += (k < bucket || (k == bucket && w < warp)) ? c : 0;
-            total += c;
+        const int excl = done + incl - c0 - c1;
+        __syncwarp();
+        s_off[2 * lane] = excl;
+        s_off[2 * lane + 1] = excl + c0;
+        __syncwarp();
+        // place
+        for (int i = lane; i < nb; i += 32) {
+            const int c = s_cls[i];
+            const int c_prev = __shfl_up_sync(kFull, c, 1);  // every lane takes part
+            const bool head = lane == 0 || c != c_prev;
+            const uint32_t heads = __ballot_sync(kFull, head);
+            int pos = 0;
+            if (head && c < kChordClasses) {
+                const uint32_t after = heads & ~below & ~(1u << lane);
+                pos = atomicAdd(&s_off[c], (after ? __ffs(after) - 1 : 32) - lane);
+            }
+            const int lead = 31 - __clz(heads & (below | (1u << lane)));
+            pos = __shfl_sync(kFull, pos, lead) + lane - lead;
+            if (c < kChordClasses) {
+                const int j = base + i;
+                int qo = static_cast<int>(static_cast<float>(j) * inv_pw);
+                int po = j - qo * F.pw;
+                if (po < 0) { po += F.pw; --qo; }
+                if (po >= F.pw) { po -= F.pw; ++qo; }
+                if (pos < cap)
+                    list[pos] = static_cast<uint32_t>(F.p_lo + po) | (static_cast<uint32_t>(F.q_lo + qo) << 16);
+                else if (a.error_word)
+                    atomicOr(a.error_word, 2);
+            }
         }
-    {
-        const uint32_t m = __match_any_sync(kFull, bucket);
-        pos += __popc(m & ((1u << lane) - 1u));
+        done += __shfl_sync(kFull, incl, 31);
+        __syncwarp();  // the counts and classes are reused by the next batch
     }
-    if (bucket < 8) s_pix[pos] = static_cast<uint32_t>(p) | (static_cast<uint32_t>(q) << 16);
-    __syncthreads();
-    const int k = warp * 32 + lane;
-    const uint32_t pq = k < total ? s_pix[k] : (static_cast<uint32_t>(a.width) | (static_cast<uint32_t>(a.height) << 16));
-    if (__all_sync(kFull, k >= total)) return;
-    float *out = a.partial + static_cast<long long>(slot) * a.slot_stride +
+    if (lane == 0) a.ray_count[r * a.n_views + vi] = min(done, cap);
+}
+
+// The march of the region schedule: CTA b of view vi (cta_begin[vi] <= b <
+// cta_begin[vi + 1]) in region blockIdx.y stages the region's march tables
+// and gives each warp the next 32 rays of the view's ray list for the region,
+// so that warp w of CTA cb marches entries (cb * warps + w) * 32 .. + 31.
+// CTAs past the end of the list return at once.
+template <int STORE, int DEPTH, int MINB, bool PAIRED>
+__global__ void __launch_bounds__(256, MINB) region_kernel(const __grid_constant__ RegionArgs a)
+{
+    extern __shared__ int32_t s_tab[];
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int b = static_cast<int>(blockIdx.x);
+    int vi = 0, hi = a.n_views - 1;  // last view whose first CTA is <= b
+    while (vi < hi) {
+        const int mid = (vi + hi + 1) >> 1;
+        if (a.cta_begin[mid] <= b) vi = mid;
+        else hi = mid - 1;
+    }
+    const int r = static_cast<int>(blockIdx.y);
+    const int count = a.ray_count[r * a.n_views + vi];
+    const int first = (b - a.cta_begin[vi]) * a.rays_per_cta;
+    if (first >= count) return;
+    const ViewDev &V = a.views[vi];
+    const RegionFrame F = region_frame(a, vi, r);
+    for (int i = 0; i < 3; ++i) {
+        const bool mirrored = (V.flags & (kFlagMirror0 << i)) != 0u;
+        const int len = F.B.hi[i] - F.B.lo[i];
+        const int src = march_table_base(a.vol.n, i) + (mirrored ? a.vol.n[i] + 2 : 0) + F.B.lo[i];
+        for (int j = threadIdx.x; j < len + 2; j += blockDim.x)
+            s_tab[i * (a.region + 2) + j] = j < len ? a.vol.mtab[src + j] : kTabSentinel;
+    }
+    if (threadIdx.x < kTabPad) s_tab[3 * (a.region + 2) + threadIdx.x] = kTabSentinel;
+    const int k = first + warp * 32 + lane;
+    const uint32_t *list = a.rays + (static_cast<long long>(r) * a.cta_begin[a.n_views] + a.cta_begin[vi]) * a.rays_per_cta;
+    const uint32_t pq = k < count ? list[k] : (static_cast<uint32_t>(a.width) | (static_cast<uint32_t>(a.height) << 16));
+    __syncthreads();  // tables staged
+    if (__all_sync(kFull, k >= count)) return;
+    float *out = a.partial + static_cast<long long>(F.slot) * a.slot_stride +
                  static_cast<long long>(a.batch_view[vi]) * a.width * a.height;
-    march_ray<STORE, DEPTH, PAIRED, true, true>(a.vol, V, B, static_cast<int>(pq & 0xffffu), static_cast<int>(pq >> 16),
+    march_ray<STORE, DEPTH, PAIRED, true, true>(a.vol, V, F.B, static_cast<int>(pq & 0xffffu), static_cast<int>(pq >> 16),
                                                 a.width, a.height, out, nullptr, a.error_word, s_tab);
 }
 
@@ -1953,13 +2063,25 @@ cudaError_t launch_touch(MarchArgs &a, uint32_t *bits, long long cells, const La
     return cudaLaunchKernel(k, L.grid, L.block, params, L.smem, stream);
 }
 
+cudaError_t launch_screen(const RegionArgs &a, cudaStream_t stream)
+{
+    if (a.n_views < 1 || a.n_views > kViewsPerRegionLaunch || !a.rays || !a.ray_count || a.rays_per_cta < 32)
+        return cudaErrorInvalidValue;
+    const long long regions = static_cast<long long>(a.nreg[0]) * a.nreg[1] * a.nreg[2];
+    if (regions < 1 || regions > 65535) return cudaErrorInvalidValue;
+    const long long ctas = (a.n_views * regions + kScreenWarps - 1) / kScreenWarps;
+    void *params[] = {const_cast<RegionArgs *>(&a)};
+    return cudaLaunchKernel(reinterpret_cast<void *>(&screen_kernel), dim3(static_cast<unsigned>(ctas)),
+                            dim3(32 * kScreenWarps), params, 0, stream);
+}
+
 cudaError_t launch_region(const RegionArgs &a, const LaunchCfg &cfg, cudaStream_t stream)
 {
     void *k = select_region(a.vol.store, cfg.depth, cfg.regcap, a.vol.paired);
     if (!k || a.n_views < 1 || a.n_views > kViewsPerRegionLaunch) return cudaErrorInvalidValue;
     const long long regions = static_cast<long long>(a.nreg[0]) * a.nreg[1] * a.nreg[2];
     const int ctas = a.cta_begin[a.n_views];
-    if (ctas < 1 || regions < 1 || regions > 65535) return cudaErrorInvalidValue;
+    if (ctas < 1 || regions < 1 || regions > 65535 || a.rays_per_cta != 32 * cfg.cta_warps) return cudaErrorInvalidValue;
     const int smem = static_cast<int>(sizeof(int32_t)) * (3 * (a.region + 2) + kTabPad);
     void *params[] = {const_cast<RegionArgs *>(&a)};
     return cudaLaunchKernel(k, dim3(static_cast<unsigned>(ctas), static_cast<unsigned>(regions)),

@@ -65,6 +65,11 @@ struct gbd_ctx {
     cudaStream_t capture_stream = nullptr;
     cudaStream_t aux[4] = {};         // side streams of multi-volume renders (created on first use)
     cudaEvent_t aux_done[4] = {};
+    // End of the march of the last region-schedule batch enqueued, on any
+    // stream: the next one waits for it, so that two batches never march side
+    // by side (each relies on its regions' records staying in L2), while a
+    // batch's copy to host memory still overlaps the next batch's march.
+    cudaEvent_t region_done = nullptr;
     int *err_word = nullptr;          // bounds-check word of checked builds
     gbd::GraphCache *graphs = nullptr;
     gbd::Server *server = nullptr;
@@ -113,8 +118,10 @@ int march_chunks(int n);
 double view_work(const Volume &vol, const ViewDev &V, int width, int height);
 // Region schedule (see RegionArgs): slots per ray, 0 when it does not apply.
 int region_slots(const Volume &vol, const LaunchCfg &cfg, const gbd_image_spec &spec, int nreg[3]);
+size_t region_scratch_bytes(const Volume &vol, const LaunchCfg &cfg, const gbd_image_spec &spec,
+                            const std::vector<ViewDev> &hv, size_t *rays_off, size_t *count_off);
 cudaError_t enqueue_regions(Ctx &ctx, const Volume &vol, const std::vector<ViewDev> &hv, const gbd_image_spec &spec,
-                            const LaunchCfg &cfg, float *dev_out, float *partial, cudaStream_t st, int *launches);
+                            const LaunchCfg &cfg, float *dev_out, char *scratch, cudaStream_t st, int *launches);
 std::vector<double> view_works(const Volume &vol, const std::vector<ViewDev> &hv, int width, int height);
 void fill_args(MarchArgs &a, const Volume &vol, const ViewDev *hv, int n, int c, const gbd_image_spec &s,
                float *out, uint32_t *samples, int *queue, const LaunchCfg &cfg, int *err_word);

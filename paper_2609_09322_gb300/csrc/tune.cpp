@@ -71,8 +71,7 @@ int time_config(Ctx &ctx, const Volume &vol, const std::vector<ViewDev> &hv, con
     char *scratch = nullptr;
     int nreg[3];
     const int slots = region_slots(vol, cfg, spec, nreg);
-    const size_t pix = static_cast<size_t>(spec.width) * spec.height * n;
-    const size_t qbytes = slots > 0 ? sizeof(float) * pix * static_cast<size_t>(slots)
+    const size_t qbytes = slots > 0 ? region_scratch_bytes(vol, cfg, spec, hv, nullptr, nullptr)
                                     : (static_cast<size_t>(n) * sizeof(int) + 255) / 256 * 256;
     cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&scratch), qbytes, st);
     if (e != cudaSuccess) return cuda_fail(e, "tune scratch");
@@ -88,7 +87,7 @@ int time_config(Ctx &ctx, const Volume &vol, const std::vector<ViewDev> &hv, con
         if (e == cudaSuccess) e = cudaEventRecord(a, st);
         int launches = 0;
         if (slots > 0 && e == cudaSuccess)
-            e = enqueue_regions(ctx, vol, hv, spec, cfg, spec.out, reinterpret_cast<float *>(scratch), st, &launches);
+            e = enqueue_regions(ctx, vol, hv, spec, cfg, spec.out, scratch, st, &launches);
         for (int c = 0; c < chunks && e == cudaSuccess && slots == 0; ++c) {
             fill_args(*args, vol, hv.data(), n, c, spec, spec.out, nullptr, reinterpret_cast<int *>(scratch), cfg,
                       ctx.err_word);

@@ -532,8 +532,9 @@ class Context:
                                                int(bool(paired)), int(bool(morton_cells))))
 
     def bounds_violations(self) -> int:
-        """Device bounds-check word of the checked library (waits for the
-        device and clears the word)."""
+        """Device error word (waits for the device and clears it): bit 0 a
+        bounds-check violation of the checked library, bit 1 a region ray
+        list that ran out of room; 0 when neither happened."""
         w = ctypes.c_int32()
         _check(self.lib, self.lib.gbd_bounds_violations(self.handle, ctypes.byref(w)))
         return int(w.value)

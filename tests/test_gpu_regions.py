@@ -89,6 +89,28 @@ def test_region_schedule_matches_whole_rays(ctx, seed, n, M, store, paired, look
         assert_parity(reg[k], oracle.render(grid, js, bs, views[k]), rel=rel, what=f"view {k} region vs oracle")
         # both schedules sit within 1e-5 of the oracle
         assert_parity(reg[k], whole[k], rel=2e-5, what=f"view {k} region vs whole ray")
+    assert ctx.bounds_violations() == 0
+    ctx.unload(vol)
+
+
+@pytest.mark.parametrize("warps", [1, 4, 8])
+def test_region_ray_lists_hold_every_crossing_ray(ctx, warps):
+    """Fine pixels (0.3-0.7 cells), stretched cells, a wide non-square
+    image zoomed in past the grid's edges, and CTAs of 1 to 8 warps: each
+    region's ray list (sized by the bound on the pixels the region's box can
+    cover) takes every crossing ray, so the images equal the whole-ray march
+    and no list overflows."""
+    grid = gen.Grid(n=(37, 29, 41), origin=(1.0, -3.0, 0.0), dx=(0.7, 1.3, 1.0), n_epochs=3, t0=0.0, dt=4.0)
+    j, beta = _fields(31, grid.n, grid.n_epochs)
+    vol = ctx.load_snapshots(grid, j, beta)
+    for fov in (20.0, 45.0):
+        views = [gen.view_from_direction(grid, d, size=112, height=72, fov=fov, c=1.1, t_obs=3.0)
+                 for d in gen.fibonacci_directions(7)]
+        whole = _batch(ctx, vol, views, region=0)
+        got = _batch(ctx, vol, views, region=16, cta_warps=warps, persistent=0)
+        for k in range(len(views)):
+            assert_parity(got[k], whole[k], rel=2e-5, what=f"{warps} warps fov {fov} view {k}")
+        assert ctx.bounds_violations() == 0
     ctx.unload(vol)
 
 
