@@ -67,7 +67,7 @@ RECORD_BYTES = {"f32": 16, "bf16": 8}
 # measured fastest on GB300 for each workload, within the autotuner's search
 # space.
 PINNED = {
-    "batched": ("4,8,8,2,1,64", "8,4,0"),
+    "batched": ("4,8,4,2,1,64", "8,4,0"),
     "batched_bf16": ("4,8,4,2,1,64", "4,4,1"),
     "time_delay": ("4,8,4,2,1,0,1", "4,4,0"),
     "time_delay_grouped": ("4,8,4,2,1,0,4", "4,2,1"),
@@ -120,7 +120,8 @@ def parse_launch(spec: str):
 
 
 def parse_layout(spec: str):
-    return ([int(x) for x in spec.split(",")] + [0])[:3] if spec else (0, 0, 0)
+    """brick, super-brick, paired[, Morton cell order] (0 where not given)."""
+    return ([int(x) for x in spec.split(",")] + [0, 0])[:4] if spec else (0, 0, 0, 0)
 
 
 # ------------------------------------------------------------------ clocks
@@ -245,10 +246,10 @@ def roofline(samples: int, bytes_per_sample: int, kernel_ms: float, traffic=None
 # ------------------------------------------------------------------ GPU timing
 def load_volume(ctx, wl, store: str, layout):
     import torch
-    brick, sbrick, paired = layout
+    brick, sbrick, paired, morton = layout
     t0 = time.perf_counter()
     vol = ctx.load_snapshots(wl["grid"], wl["j"], wl["beta"], store=store, brick=brick, super_brick=sbrick,
-                             paired=bool(paired))
+                             paired=bool(paired), morton_cells=bool(morton))
     torch.cuda.synchronize()
     return vol, ctx.volume_info(vol), time.perf_counter() - t0
 
@@ -323,7 +324,8 @@ def march_entry(ctx, wl, vol, info, launch, stream, steps, warmup, world, dev, *
                    "images_per_step": n_views, "cell_samples_per_step": samples, "volume_bytes": info["bytes"],
                    "l2": L2_NOTE % (info["bytes"] / 1e9),
                    "layout": f"brick {info['brick']}, super-brick {info['super_brick']}"
-                             + (", paired snapshots" if info.get("paired") else ""),
+                             + (", paired snapshots" if info.get("paired") else "")
+                             + (", Morton cell order" if info.get("morton_cells") else ""),
                    "launch": "default" if per_image else
                              {k: launch[k] for k in ("packet", "cta_warps", "depth", "persistent", "regcap",
                                                      "region", "group")}},
@@ -390,7 +392,7 @@ def run_suite(args, rank: int, world: int):
         # float32 per-image march (default layout and launch)
         for key, store, form in (("batched_bf16", "bf16", "batched_bf16"), ("batched_f32_per_image", "f32", None)):
             launch = parse_launch(PINNED[form][0]) if form else None
-            layout = parse_layout(PINNED[form][1]) if form else (0, 0, 0)
+            layout = parse_layout(PINNED[form][1]) if form else (0, 0, 0, 0)
             vol, info, _ = load_volume(ctx, wl, store, layout)
             e, img, _ = march_entry(ctx, wl, vol, info, launch, stream, args.steps if form else max(3, min(args.steps, 5)),
                                     args.warmup if form else 3, world, dev, per_image=form is None, clk=clk)
@@ -418,7 +420,7 @@ def run_suite(args, rank: int, world: int):
                                  ("time_delay_bf16", "bf16", "time_delay_bf16"),
                                  ("time_delay_f32_per_image", "f32", None)):
             launch = parse_launch(PINNED[form][0]) if form else None
-            layout = parse_layout(PINNED[form][1]) if form else (0, 0, 0)
+            layout = parse_layout(PINNED[form][1]) if form else (0, 0, 0, 0)
             vol, info, _ = load_volume(ctx, wl, store, layout)
             e, img, _ = march_entry(ctx, wl, vol, info, launch, stream, args.steps if form else 10, args.warmup,
                                     world, dev, per_image=form is None, clk=clk)
@@ -435,7 +437,7 @@ def run_suite(args, rank: int, world: int):
         wl_host = None
         for key, store, form in (("precision_bf16", "bf16", "precision"), ("precision_f32_per_image", "f32", None)):
             launch = parse_launch(PINNED[form][0]) if form else None
-            layout = parse_layout(PINNED[form][1]) if form else (0, 0, 0)
+            layout = parse_layout(PINNED[form][1]) if form else (0, 0, 0, 0)
             vol, info, _ = load_volume(ctx, wl, store, layout)
             e, img, _ = march_entry(ctx, wl, vol, info, launch, stream, args.steps if form else 10, args.warmup,
                                     world, dev, per_image=form is None, clk=clk)
@@ -572,13 +574,14 @@ def run_gpu(args, rank: int, world: int):
         g = wl["grid"]
         cut = g.n[0] // 2
         halves = []
-        brick, sbrick, paired = layout
+        brick, sbrick, paired, morton = layout
         for lo, hi in ((0, cut), (cut, g.n[0])):
             sub = type(g)(n=(hi - lo, g.n[1], g.n[2]), origin=(g.origin[0] + lo * g.dx[0], g.origin[1], g.origin[2]),
                           dx=g.dx, n_epochs=g.n_epochs, t0=g.t0, dt=g.dt)
             halves.append(ctx.load_snapshots(sub, np.ascontiguousarray(wl["j"][..., lo:hi]),
                                              np.ascontiguousarray(wl["beta"][..., lo:hi, :]), store=wl["store"],
-                                             brick=brick, super_brick=sbrick, paired=bool(paired)))
+                                             brick=brick, super_brick=sbrick, paired=bool(paired),
+                                             morton_cells=bool(morton)))
 
         def step():
             ctx.render_labelled(halves, views, out=out, launch=launch, stream=stream)
@@ -664,7 +667,8 @@ def run_gpu(args, rank: int, world: int):
                    "volume_bytes": info["bytes"], "l2": L2_NOTE % (info["bytes"] / 1e9),
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "layout": f"brick {info['brick']}, super-brick {info['super_brick']}"
-                             + (", paired snapshots" if info.get("paired") else ""),
+                             + (", paired snapshots" if info.get("paired") else "")
+                             + (", Morton cell order" if info.get("morton_cells") else ""),
                    "launch": ({k: tuned[k] for k in ("packet", "cta_warps", "depth", "persistent", "regcap", "region", "group") if k in tuned}
                               if tuned else "default")},
         "images_per_s": round(world * n_views / (ms_per_step * 1e-3), 2),

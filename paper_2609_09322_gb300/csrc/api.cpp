@@ -582,90 +582,106 @@ static std::vector<int> direction_order(const std::vector<ViewDev> &hv)
     return order;
 }
 
-// Scratch of a region-schedule batch of the views hv: the partial slots
-// (slots * n * W * H floats), then the ray lists and their counts, which each
-// launch of the batch reuses in turn (room for the launch with the most CTAs:
-// at most kViewsPerRegionLaunch views of the most CTAs per region).
-size_t region_scratch_bytes(const Volume &vol, const LaunchCfg &cfg, const gbd_image_spec &spec,
-                            const std::vector<ViewDev> &hv, size_t *rays_off, size_t *count_off)
+// Layout of a region-schedule batch's scratch: the partial slots (slots * n *
+// W * H floats), the ray lists (room for ctas_per_view CTAs of rays per view
+// and region) and their counts, and the region tables: the views in march
+// order, their projections and their images in the batch, which the caller
+// uploads from `tables` before the batch first runs.
+RegionPlan region_plan(const Volume &vol, const LaunchCfg &cfg, const gbd_image_spec &spec,
+                       const std::vector<ViewDev> &hv)
 {
-    int nreg[3];
-    const int slots = region_slots(vol, cfg, spec, nreg);
-    if (slots <= 0) return 0;
+    RegionPlan P;
+    P.slots = region_slots(vol, cfg, spec, P.nreg);
+    if (P.slots <= 0) return P;
     const size_t n = hv.size();
-    const size_t regions = static_cast<size_t>(nreg[0]) * nreg[1] * nreg[2];
-    size_t per_view = 0;
-    for (const ViewDev &V : hv) per_view = std::max(per_view, static_cast<size_t>(region_ctas(region_proj(V), cfg.region, cfg)));
-    const size_t views = std::min(n, static_cast<size_t>(kViewsPerRegionLaunch));
-    const size_t pbytes = (sizeof(float) * static_cast<size_t>(spec.width) * spec.height * n * slots + 255) / 256 * 256;
-    const size_t rbytes = (sizeof(uint32_t) * regions * views * per_view * 32 * cfg.cta_warps + 255) / 256 * 256;
-    const size_t cbytes = (sizeof(int) * regions * views + 255) / 256 * 256;
-    if (rays_off) *rays_off = pbytes;
-    if (count_off) *count_off = pbytes + rbytes;
-    return pbytes + rbytes + cbytes;
+    auto up = [](size_t b) { return (b + 255) / 256 * 256; };
+    P.regions = static_cast<size_t>(P.nreg[0]) * P.nreg[1] * P.nreg[2];
+    size_t per_view = 1;
+    std::vector<RegionProj> proj(n);
+    const std::vector<int> order = direction_order(hv);
+    for (size_t k = 0; k < n; ++k) {
+        proj[k] = region_proj(hv[order[k]]);
+        per_view = std::max(per_view, static_cast<size_t>(region_ctas(proj[k], cfg.region, cfg)));
+    }
+    P.ctas_per_view = static_cast<int>(std::min<size_t>(per_view, 0x7fffffff));
+    const size_t pbytes = up(sizeof(float) * static_cast<size_t>(spec.width) * spec.height * n * P.slots);
+    const size_t rbytes = up(sizeof(uint32_t) * P.regions * n * per_view * 32 * cfg.cta_warps);
+    const size_t cbytes = up(sizeof(int) * P.regions * n);
+    P.rays_off = pbytes;
+    P.count_off = P.rays_off + rbytes;
+    P.views_off = P.count_off + cbytes;
+    P.proj_off = P.views_off + up(sizeof(ViewDev) * n);
+    P.image_off = P.proj_off + up(sizeof(RegionProj) * n);
+    P.total = P.image_off + up(sizeof(int) * n);
+    P.tables.assign(P.total - P.views_off, 0);
+    char *t = P.tables.data();
+    for (size_t k = 0; k < n; ++k) {
+        std::memcpy(t + (P.views_off - P.views_off) + k * sizeof(ViewDev), &hv[order[k]], sizeof(ViewDev));
+        std::memcpy(t + (P.proj_off - P.views_off) + k * sizeof(RegionProj), &proj[k], sizeof(RegionProj));
+        const int img = order[k];
+        std::memcpy(t + (P.image_off - P.views_off) + k * sizeof(int), &img, sizeof(int));
+    }
+    return P;
 }
 
-// Enqueues a region-schedule batch on st: clear the partial slots; per
-// kViewsPerRegionLaunch views in direction order, list each region's crossing
-// rays by chord length and march them (two launches over all regions); then
-// add up the slots into dev_out.  scratch holds region_scratch_bytes.
-cudaError_t enqueue_regions(Ctx &ctx, const Volume &vol, const std::vector<ViewDev> &hv, const gbd_image_spec &spec,
-                            const LaunchCfg &cfg, float *dev_out, char *scratch, cudaStream_t st, int *launches)
+cudaError_t upload_region_tables(const RegionPlan &P, char *scratch, cudaStream_t st)
 {
-    int nreg[3];
-    const int slots = region_slots(vol, cfg, spec, nreg);
+    return cudaMemcpyAsync(scratch + P.views_off, P.tables.data(), P.tables.size(), cudaMemcpyHostToDevice, st);
+}
+
+// Enqueues a region-schedule batch on st (its tables already uploaded): clear
+// the partial slots, list each region's crossing rays of every view by chord
+// length (one screen_kernel launch), march them region by region (one
+// region_kernel launch over all views), then add up each image's slots into
+// dev_out (reduce_kernel, kImagesPerReduce images per launch).
+cudaError_t enqueue_regions(Ctx &ctx, const Volume &vol, const std::vector<ViewDev> &hv, const RegionPlan &P,
+                            const gbd_image_spec &spec, const LaunchCfg &cfg, float *dev_out, char *scratch,
+                            cudaStream_t st, int *launches)
+{
     const int n = static_cast<int>(hv.size());
     const long long pix = static_cast<long long>(spec.width) * spec.height;
     const long long slot_stride = pix * n;
-    size_t rays_off = 0, count_off = 0;
-    region_scratch_bytes(vol, cfg, spec, hv, &rays_off, &count_off);
     float *partial = reinterpret_cast<float *>(scratch);
-    cudaError_t e = cudaMemsetAsync(partial, 0, sizeof(float) * static_cast<size_t>(slot_stride) * slots, st);
-    auto a = std::make_unique<RegionArgs>();
-    const std::vector<int> order = direction_order(hv);
     *launches = 0;
-    for (int first = 0; first < n && e == cudaSuccess; first += kViewsPerRegionLaunch) {
-        const int cnt = std::min(kViewsPerRegionLaunch, n - first);
-        std::memset(a.get(), 0, sizeof(RegionArgs));
-        a->vol = vol_dev(vol);
-        a->n_views = cnt;
-        a->width = spec.width;
-        a->height = spec.height;
-        a->packet_w = cfg.packet_w;
-        a->packet_h = cfg.packet_h;
-        a->region = cfg.region;
-        for (int i = 0; i < 3; ++i) a->nreg[i] = nreg[i];
-        a->partial = partial;
-        a->slot_stride = slot_stride;
-        a->error_word = ctx.err_word;
-        a->rays = reinterpret_cast<uint32_t *>(scratch + rays_off);
-        a->ray_count = reinterpret_cast<int *>(scratch + count_off);
-        a->rays_per_cta = 32 * cfg.cta_warps;
-        long long total = 0;
-        for (int v = 0; v < cnt; ++v) {
-            a->batch_view[v] = order[first + v];
-            a->views[v] = hv[order[first + v]];
-            a->proj[v] = region_proj(a->views[v]);
-            a->cta_begin[v] = static_cast<int>(total);
-            total += region_ctas(a->proj[v], cfg.region, cfg);
-        }
-        if (total > 0x7fffffffLL) return cudaErrorInvalidValue;
-        a->cta_begin[cnt] = static_cast<int>(total);
-        e = launch_screen(*a, st);
-        if (e == cudaSuccess) e = launch_region(*a, cfg, st);
-        *launches += 2;
-    }
+    if (P.slots <= 0 || n < 1) return cudaErrorInvalidValue;
+    cudaError_t e = cudaMemsetAsync(partial, 0, sizeof(float) * static_cast<size_t>(slot_stride) * P.slots, st);
+    RegionArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.vol = vol_dev(vol);
+    a.n_views = n;
+    a.width = spec.width;
+    a.height = spec.height;
+    a.packet_w = cfg.packet_w;
+    a.packet_h = cfg.packet_h;
+    a.region = cfg.region;
+    for (int i = 0; i < 3; ++i) a.nreg[i] = P.nreg[i];
+    a.partial = partial;
+    a.slot_stride = slot_stride;
+    a.error_word = ctx.err_word;
+    a.views = reinterpret_cast<const ViewDev *>(scratch + P.views_off);
+    a.proj = reinterpret_cast<const RegionProj *>(scratch + P.proj_off);
+    a.image = reinterpret_cast<const int *>(scratch + P.image_off);
+    a.rays = reinterpret_cast<uint32_t *>(scratch + P.rays_off);
+    a.ray_count = reinterpret_cast<int *>(scratch + P.count_off);
+    a.rays_per_cta = 32 * cfg.cta_warps;
+    a.ctas_per_view = P.ctas_per_view;
+    if (e == cudaSuccess) e = launch_screen(a, st);
+    if (e == cudaSuccess) e = launch_region(a, cfg, st);
+    *launches += 2;
     auto r = std::make_unique<ReduceArgs>();
-    for (int first = 0; first < n && e == cudaSuccess; first += kViewsPerRegionLaunch) {
-        const int cnt = std::min(kViewsPerRegionLaunch, n - first);
+    for (int first = 0; first < n && e == cudaSuccess; first += kImagesPerReduce) {
+        const int cnt = std::min(kImagesPerReduce, n - first);
         std::memset(r.get(), 0, sizeof(ReduceArgs));
-        r->out = dev_out + first * pix;
-        r->partial = partial + first * pix;
+        r->out = dev_out;
+        r->partial = partial;
         r->slot_stride = slot_stride;
         r->pix_per_view = pix;
         r->n_views = cnt;
-        r->n_slots = slots;
-        for (int v = 0; v < cnt; ++v) r->prefactor[v] = hv[first + v].prefactor;
+        r->n_slots = P.slots;
+        for (int v = 0; v < cnt; ++v) {
+            r->image[v] = first + v;
+            r->prefactor[v] = hv[first + v].prefactor;
+        }
         e = launch_reduce(*r, st);
         ++*launches;
     }
@@ -684,14 +700,16 @@ int render_direct(Ctx &ctx, const Volume &vol, const std::vector<ViewDev> &hv, c
     int nreg[3];
     const int slots = region_slots(vol, cfg, spec, nreg);
     if (slots > 0) {
-        const size_t pbytes = region_scratch_bytes(vol, cfg, spec, hv, nullptr, nullptr);
+        const RegionPlan plan = region_plan(vol, cfg, spec, hv);
+        const size_t pbytes = plan.total;
         const size_t total = pbytes + (spec.out_on_host ? pix * sizeof(float) : 0);
         cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&scratch), total, st);
         if (e != cudaSuccess) return cuda_fail(e, "region scratch");
         float *dev_out = spec.out_on_host ? reinterpret_cast<float *>(scratch + pbytes) : spec.out;
         int launches = 0;
-        e = cudaStreamWaitEvent(st, ctx.region_done, 0);
-        if (e == cudaSuccess) e = enqueue_regions(ctx, vol, hv, spec, cfg, dev_out, scratch, st, &launches);
+        e = upload_region_tables(plan, scratch, st);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ctx.region_done, 0);
+        if (e == cudaSuccess) e = enqueue_regions(ctx, vol, hv, plan, spec, cfg, dev_out, scratch, st, &launches);
         if (e == cudaSuccess) e = cudaEventRecord(ctx.region_done, st);
         if (e == cudaSuccess && spec.out_on_host)
             e = cudaMemcpyAsync(spec.out, dev_out, pix * sizeof(float), cudaMemcpyDeviceToHost, st);
@@ -843,10 +861,13 @@ static int build_region_graph(Ctx &ctx, const Volume &vol, const GraphKey &key, 
                               const std::vector<ViewDev> &hv, int slots, GraphEntry &g)
 {
     const size_t pix = static_cast<size_t>(spec.width) * spec.height * key.n;
-    const size_t pbytes = region_scratch_bytes(vol, key.cfg, spec, hv, nullptr, nullptr);
+    const RegionPlan plan = region_plan(vol, key.cfg, spec, hv);
+    const size_t pbytes = plan.total;
     const size_t total = pbytes + (spec.out_on_host ? pix * sizeof(float) : 0);
     cudaError_t e = cudaMalloc(reinterpret_cast<void **>(&g.d_scratch), total);
     if (e != cudaSuccess) return cuda_fail(e, "region batch scratch");
+    e = cudaMemcpy(g.d_scratch + plan.views_off, plan.tables.data(), plan.tables.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(e, "region tables");
     e = cudaEventCreateWithFlags(&g.done, cudaEventDisableTiming);
     if (e != cudaSuccess) return cuda_fail(e, "batch event");
     float *dev_out = spec.out_on_host ? reinterpret_cast<float *>(g.d_scratch + pbytes) : spec.out;
@@ -854,7 +875,7 @@ static int build_region_graph(Ctx &ctx, const Volume &vol, const GraphKey &key, 
     cudaStream_t cap = ctx.capture_stream;
     e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return cuda_fail(e, "begin capture");
-    cudaError_t e2 = enqueue_regions(ctx, vol, hv, spec, key.cfg, dev_out, g.d_scratch, cap, &g.region_launches);
+    cudaError_t e2 = enqueue_regions(ctx, vol, hv, plan, spec, key.cfg, dev_out, g.d_scratch, cap, &g.region_launches);
     e = cudaStreamEndCapture(cap, &g.graph);
     if (e2 != cudaSuccess) return cuda_fail(e2, "capture region batch");
     if (e != cudaSuccess) return cuda_fail(e, "end capture");

@@ -138,8 +138,9 @@ static_assert(sizeof(MarchArgs) <= 32764, "march launch arguments exceed the ker
 // views' rays that cross it while its records sit in L2, and each ray's sum
 // over the region goes to partial slot s(r), the sum of r's region coordinates
 // in the march frame, which grows by one from region to region along a ray.
-// A reduction then adds each ray's slots in order.
-constexpr int kViewsPerRegionLaunch = 96;
+// A reduction then adds each ray's slots in order, kImagesPerReduce images
+// per launch.
+constexpr int kImagesPerReduce = 96;
 
 // Pixel coordinates of a point g of a view's march frame: p = ip . g + p0,
 // q = iq . g + q0 (the first two rows of the inverse of [gu gv a]).
@@ -151,40 +152,45 @@ struct RegionProj {
     float g0f[3], guf[3], gvf[3];
 };
 
+// The views of a region-schedule batch live in device memory (the region
+// tables), in march order: all of them go in one launch, so that the rays of
+// every view that crosses a region are marched while its records are in L2.
 struct RegionArgs {
     VolDev vol;
-    int n_views;              // views in this launch, 1 .. kViewsPerRegionLaunch
+    int n_views;              // views of the batch
     int width, height;
     int packet_w, packet_h;
     int region;               // region edge in cells
     int nreg[3];              // regions per axis
-    float *partial;           // slot s of batch view b at partial + s * slot_stride + b * width * height
+    float *partial;           // slot s of batch image b at partial + s * slot_stride + b * width * height
     long long slot_stride;    // floats per slot
     int *error_word;
+    const ViewDev *views;     // n_views views in march order (by direction)
+    const RegionProj *proj;   // their projections
+    const int *image;         // each one's image in the batch
     // Ray lists (written by screen_kernel, read by region_kernel): the pixels
     // (p | q << 16) of view v whose rays cross region r, longest chord first,
-    // at rays + (r * cta_begin[n_views] + cta_begin[v]) * rays_per_cta, and
-    // their number at ray_count[r * n_views + v].  Each list has room for all
-    // of the view's CTAs' rays in one region.
+    // at rays + (r * n_views + v) * ctas_per_view * rays_per_cta, and their
+    // number at ray_count[r * n_views + v].  Each list has room for every
+    // pixel that the region's box can cover in any of the views.
     uint32_t *rays;
     int *ray_count;
     int rays_per_cta;         // 32 * warps per CTA of region_kernel
-    int cta_begin[kViewsPerRegionLaunch + 1];  // CTAs of each view in one region (blockIdx.x)
-    int batch_view[kViewsPerRegionLaunch];     // the view's index in the batch
-    RegionProj proj[kViewsPerRegionLaunch];
-    ViewDev views[kViewsPerRegionLaunch];
+    int ctas_per_view;        // CTAs of each view in one region (blockIdx.x)
 };
-static_assert(sizeof(RegionArgs) <= 32764, "region launch arguments exceed the kernel parameter limit");
 
-// out[v][pixel] = prefactor[v] * (sum over slots of partial, in slot order).
+// For the launch's views v: out[b][pixel] = prefactor[v] * (sum over slots of
+// partial[slot][b][pixel], in slot order), b = image[v] the view's image in the
+// batch.
 struct ReduceArgs {
-    float *out;               // this launch's first image
-    const float *partial;     // slot 0 of this launch's first image
+    float *out;               // the batch's first image
+    const float *partial;     // slot 0 of the batch's first image
     long long slot_stride;    // floats per slot
     long long pix_per_view;
     int n_views;
     int n_slots;
-    float prefactor[kViewsPerRegionLaunch];
+    int image[kImagesPerReduce];
+    float prefactor[kImagesPerReduce];
 };
 
 // One request of a served wave: its own volume, view, image and outputs.
@@ -241,9 +247,9 @@ cudaError_t launch_touch(MarchArgs &a, uint32_t *bits, long long cells, const La
 cudaError_t launch_vector(MarchArgs &a, int n_chan, const LaunchCfg &cfg, int num_sms, const double *work,
                           cudaStream_t stream);
 // Region schedule: the caller has filled everything but the grid, which
-// launch_screen (one CTA per view and region) and launch_region derive from
-// cta_begin and the region counts.  launch_screen writes the ray lists that
-// the following launch_region of the same arguments marches.
+// launch_screen (a warp per view and region) and launch_region (ctas_per_view
+// x views x regions) derive from the counts.  launch_screen writes the ray
+// lists that the following launch_region of the same arguments marches.
 cudaError_t launch_screen(const RegionArgs &a, cudaStream_t stream);
 cudaError_t launch_region(const RegionArgs &a, const LaunchCfg &cfg, cudaStream_t stream);
 cudaError_t launch_reduce(const ReduceArgs &a, cudaStream_t stream);

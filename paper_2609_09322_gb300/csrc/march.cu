@@ -1714,7 +1714,7 @@ __global__ void __launch_bounds__(32 * kScreenWarps) screen_kernel(const __grid_
     const ViewDev &V = a.views[vi];
     const RegionProj &P = a.proj[vi];
     const RegionFrame F = region_frame(a, vi, r);
-    const int cap = (a.cta_begin[vi + 1] - a.cta_begin[vi]) * a.rays_per_cta;
+    const int cap = a.ctas_per_view * a.rays_per_cta;
     const int n_pix = F.pw * F.qh;
     const int nc = (n_pix + 31) & ~31;  // the whole warp takes each step
     const float inv_pw = F.pw > 0 ? 1.0f / static_cast<float>(F.pw) : 0.f;
@@ -1732,7 +1732,7 @@ __global__ void __launch_bounds__(32 * kScreenWarps) screen_kernel(const __grid_
     }
     const float cls_scale = static_cast<float>(kChordClasses) / smax;
     const float win_lo = V.win_lo, win_hi = V.win_hi;
-    uint32_t *list = a.rays + (static_cast<long long>(r) * a.cta_begin[a.n_views] + a.cta_begin[vi]) * a.rays_per_cta;
+    uint32_t *list = a.rays + (static_cast<long long>(r) * a.n_views + vi) * cap;
     const uint32_t below = (1u << lane) - 1u;
     int done = 0;
     for (int base = 0; base < nc; base += kScreenBatch) {
@@ -1817,27 +1817,21 @@ __global__ void __launch_bounds__(32 * kScreenWarps) screen_kernel(const __grid_
     if (lane == 0) a.ray_count[r * a.n_views + vi] = min(done, cap);
 }
 
-// The march of the region schedule: CTA b of view vi (cta_begin[vi] <= b <
-// cta_begin[vi + 1]) in region blockIdx.y stages the region's march tables
-// and gives each warp the next 32 rays of the view's ray list for the region,
-// so that warp w of CTA cb marches entries (cb * warps + w) * 32 .. + 31.
-// CTAs past the end of the list return at once.
+// The march of the region schedule: CTA (blockIdx.x) of view blockIdx.y in
+// region blockIdx.z stages the region's march tables and gives each warp the
+// next 32 rays of the view's ray list for the region, so that warp w of CTA cb
+// marches entries (cb * warps + w) * 32 .. + 31.  CTAs past the end of the
+// list return at once.
 template <int STORE, int DEPTH, int MINB, bool PAIRED>
 __global__ void __launch_bounds__(256, MINB) region_kernel(const __grid_constant__ RegionArgs a)
 {
     extern __shared__ int32_t s_tab[];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
-    const int b = static_cast<int>(blockIdx.x);
-    int vi = 0, hi = a.n_views - 1;  // last view whose first CTA is <= b
-    while (vi < hi) {
-        const int mid = (vi + hi + 1) >> 1;
-        if (a.cta_begin[mid] <= b) vi = mid;
-        else hi = mid - 1;
-    }
-    const int r = static_cast<int>(blockIdx.y);
-    const int count = a.ray_count[r * a.n_views + vi];
-    const int first = (b - a.cta_begin[vi]) * a.rays_per_cta;
+    const int vi = static_cast<int>(blockIdx.y);
+    const int r = static_cast<int>(blockIdx.z);
+    const int count = __ldg(a.ray_count + r * a.n_views + vi);
+    const int first = static_cast<int>(blockIdx.x) * a.rays_per_cta;
     if (first >= count) return;
     const ViewDev &V = a.views[vi];
     const RegionFrame F = region_frame(a, vi, r);
@@ -1850,22 +1844,25 @@ __global__ void __launch_bounds__(256, MINB) region_kernel(const __grid_constant
     }
     if (threadIdx.x < kTabPad) s_tab[3 * (a.region + 2) + threadIdx.x] = kTabSentinel;
     const int k = first + warp * 32 + lane;
-    const uint32_t *list = a.rays + (static_cast<long long>(r) * a.cta_begin[a.n_views] + a.cta_begin[vi]) * a.rays_per_cta;
-    const uint32_t pq = k < count ? list[k] : (static_cast<uint32_t>(a.width) | (static_cast<uint32_t>(a.height) << 16));
+    const uint32_t *list = a.rays + (static_cast<long long>(r) * a.n_views + vi) * a.ctas_per_view * a.rays_per_cta;
+    const uint32_t pq = k < count ? __ldg(list + k) : (static_cast<uint32_t>(a.width) | (static_cast<uint32_t>(a.height) << 16));
     __syncthreads();  // tables staged
     if (__all_sync(kFull, k >= count)) return;
     float *out = a.partial + static_cast<long long>(F.slot) * a.slot_stride +
-                 static_cast<long long>(a.batch_view[vi]) * a.width * a.height;
+                 static_cast<long long>(a.image[vi]) * a.width * a.height;
     march_ray<STORE, DEPTH, PAIRED, true, true>(a.vol, V, F.B, static_cast<int>(pq & 0xffffu), static_cast<int>(pq >> 16),
                                                 a.width, a.height, out, nullptr, a.error_word, s_tab);
 }
 
-// out = prefactor * (partial slots summed in slot order, compensated).
+// One view per blockIdx.y.
 __global__ void __launch_bounds__(256) reduce_kernel(const __grid_constant__ ReduceArgs a)
 {
-    const long long n = a.pix_per_view * a.n_views;
-    for (long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
-         i += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const int v = static_cast<int>(blockIdx.y);
+    const long long img = static_cast<long long>(a.image[v]) * a.pix_per_view;
+    const float pre = a.prefactor[v];
+    for (long long px = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; px < a.pix_per_view;
+         px += static_cast<long long>(gridDim.x) * blockDim.x) {
+        const long long i = img + px;
         float acc = 0.f, comp = 0.f;
         for (int s = 0; s < a.n_slots; ++s) {
             const float y = a.partial[static_cast<long long>(s) * a.slot_stride + i] - comp;
@@ -1873,7 +1870,7 @@ __global__ void __launch_bounds__(256) reduce_kernel(const __grid_constant__ Red
             comp = (t - acc) - y;
             acc = t;
         }
-        a.out[i] = a.prefactor[static_cast<int>(i / a.pix_per_view)] * acc;
+        a.out[i] = pre * acc;
     }
 }
 
@@ -2065,10 +2062,10 @@ cudaError_t launch_touch(MarchArgs &a, uint32_t *bits, long long cells, const La
 
 cudaError_t launch_screen(const RegionArgs &a, cudaStream_t stream)
 {
-    if (a.n_views < 1 || a.n_views > kViewsPerRegionLaunch || !a.rays || !a.ray_count || a.rays_per_cta < 32)
-        return cudaErrorInvalidValue;
     const long long regions = static_cast<long long>(a.nreg[0]) * a.nreg[1] * a.nreg[2];
-    if (regions < 1 || regions > 65535) return cudaErrorInvalidValue;
+    if (a.n_views < 1 || a.n_views > 65535 || !a.rays || !a.ray_count || !a.views || !a.proj || a.rays_per_cta < 32 ||
+        a.ctas_per_view < 1 || regions < 1 || regions > 65535)
+        return cudaErrorInvalidValue;
     const long long ctas = (a.n_views * regions + kScreenWarps - 1) / kScreenWarps;
     void *params[] = {const_cast<RegionArgs *>(&a)};
     return cudaLaunchKernel(reinterpret_cast<void *>(&screen_kernel), dim3(static_cast<unsigned>(ctas)),
@@ -2078,24 +2075,27 @@ cudaError_t launch_screen(const RegionArgs &a, cudaStream_t stream)
 cudaError_t launch_region(const RegionArgs &a, const LaunchCfg &cfg, cudaStream_t stream)
 {
     void *k = select_region(a.vol.store, cfg.depth, cfg.regcap, a.vol.paired);
-    if (!k || a.n_views < 1 || a.n_views > kViewsPerRegionLaunch) return cudaErrorInvalidValue;
     const long long regions = static_cast<long long>(a.nreg[0]) * a.nreg[1] * a.nreg[2];
-    const int ctas = a.cta_begin[a.n_views];
-    if (ctas < 1 || regions < 1 || regions > 65535 || a.rays_per_cta != 32 * cfg.cta_warps) return cudaErrorInvalidValue;
+    if (!k || a.n_views < 1 || a.n_views > 65535 || regions < 1 || regions > 65535 || a.ctas_per_view < 1 ||
+        a.rays_per_cta != 32 * cfg.cta_warps || !a.image)
+        return cudaErrorInvalidValue;
     const int smem = static_cast<int>(sizeof(int32_t)) * (3 * (a.region + 2) + kTabPad);
     void *params[] = {const_cast<RegionArgs *>(&a)};
-    return cudaLaunchKernel(k, dim3(static_cast<unsigned>(ctas), static_cast<unsigned>(regions)),
+    return cudaLaunchKernel(k, dim3(static_cast<unsigned>(a.ctas_per_view), static_cast<unsigned>(a.n_views),
+                                    static_cast<unsigned>(regions)),
                             dim3(32 * cfg.cta_warps), params, smem, stream);
 }
 
 cudaError_t launch_reduce(const ReduceArgs &a, cudaStream_t stream)
 {
-    const long long n = a.pix_per_view * a.n_views;
-    if (n < 1) return cudaSuccess;
-    const long long blocks = std::min<long long>((n + 255) / 256, 152LL * 16);
+    if (a.n_views < 1 || a.pix_per_view < 1) return cudaSuccess;
+    if (a.n_views > kImagesPerReduce) return cudaErrorInvalidValue;
+    const long long per_view = std::max<long long>(1, 152LL * 16 / a.n_views);
+    const long long blocks = std::min<long long>((a.pix_per_view + 255) / 256, per_view);
     void *params[] = {const_cast<ReduceArgs *>(&a)};
-    return cudaLaunchKernel(reinterpret_cast<void *>(&reduce_kernel), dim3(static_cast<unsigned>(blocks)), dim3(256),
-                            params, 0, stream);
+    return cudaLaunchKernel(reinterpret_cast<void *>(&reduce_kernel),
+                            dim3(static_cast<unsigned>(blocks), static_cast<unsigned>(a.n_views)), dim3(256), params,
+                            0, stream);
 }
 
 cudaError_t plan_march(MarchArgs &a, const LaunchCfg &cfg, int num_sms, const double *work, KernelLaunch &L)

@@ -118,10 +118,19 @@ int march_chunks(int n);
 double view_work(const Volume &vol, const ViewDev &V, int width, int height);
 // Region schedule (see RegionArgs): slots per ray, 0 when it does not apply.
 int region_slots(const Volume &vol, const LaunchCfg &cfg, const gbd_image_spec &spec, int nreg[3]);
-size_t region_scratch_bytes(const Volume &vol, const LaunchCfg &cfg, const gbd_image_spec &spec,
-                            const std::vector<ViewDev> &hv, size_t *rays_off, size_t *count_off);
-cudaError_t enqueue_regions(Ctx &ctx, const Volume &vol, const std::vector<ViewDev> &hv, const gbd_image_spec &spec,
-                            const LaunchCfg &cfg, float *dev_out, char *scratch, cudaStream_t st, int *launches);
+struct RegionPlan {
+    int slots = 0, nreg[3] = {0, 0, 0};
+    size_t regions = 0;
+    int ctas_per_view = 0;
+    size_t rays_off = 0, count_off = 0, views_off = 0, proj_off = 0, image_off = 0, total = 0;
+    std::vector<char> tables;  // host image of the scratch from views_off to total
+};
+RegionPlan region_plan(const Volume &vol, const LaunchCfg &cfg, const gbd_image_spec &spec,
+                       const std::vector<ViewDev> &hv);
+cudaError_t upload_region_tables(const RegionPlan &P, char *scratch, cudaStream_t st);
+cudaError_t enqueue_regions(Ctx &ctx, const Volume &vol, const std::vector<ViewDev> &hv, const RegionPlan &P,
+                            const gbd_image_spec &spec, const LaunchCfg &cfg, float *dev_out, char *scratch,
+                            cudaStream_t st, int *launches);
 std::vector<double> view_works(const Volume &vol, const std::vector<ViewDev> &hv, int width, int height);
 void fill_args(MarchArgs &a, const Volume &vol, const ViewDev *hv, int n, int c, const gbd_image_spec &s,
                float *out, uint32_t *samples, int *queue, const LaunchCfg &cfg, int *err_word);

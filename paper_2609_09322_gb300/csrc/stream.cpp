@@ -381,16 +381,19 @@ extern "C" int gbd_render_labelled(gbd_ctx *ctx, const gbd_volume *vols, int32_t
         // add the sub-domains' images in order (prefactors already applied)
         auto r = std::make_unique<ReduceArgs>();
         const long long per = static_cast<long long>(spec->width) * spec->height;
-        for (int first = 0; first < n && e == cudaSuccess; first += kViewsPerRegionLaunch) {
-            const int cnt = std::min(kViewsPerRegionLaunch, n - first);
+        for (int first = 0; first < n && e == cudaSuccess; first += kImagesPerReduce) {
+            const int cnt = std::min(kImagesPerReduce, n - first);
             std::memset(r.get(), 0, sizeof(ReduceArgs));
-            r->out = spec->out + first * per;
-            r->partial = parts + first * per;
+            r->out = spec->out;
+            r->partial = parts;
             r->slot_stride = static_cast<long long>(pix);
             r->pix_per_view = per;
             r->n_views = cnt;
             r->n_slots = n_vols;
-            for (int v = 0; v < cnt; ++v) r->prefactor[v] = 1.0f;
+            for (int v = 0; v < cnt; ++v) {
+                r->image[v] = first + v;
+                r->prefactor[v] = 1.0f;
+            }
             e = launch_reduce(*r, st);
             ++launches;
         }

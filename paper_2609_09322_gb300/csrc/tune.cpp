@@ -71,10 +71,11 @@ int time_config(Ctx &ctx, const Volume &vol, const std::vector<ViewDev> &hv, con
     char *scratch = nullptr;
     int nreg[3];
     const int slots = region_slots(vol, cfg, spec, nreg);
-    const size_t qbytes = slots > 0 ? region_scratch_bytes(vol, cfg, spec, hv, nullptr, nullptr)
-                                    : (static_cast<size_t>(n) * sizeof(int) + 255) / 256 * 256;
+    const RegionPlan plan = slots > 0 ? region_plan(vol, cfg, spec, hv) : RegionPlan();
+    const size_t qbytes = slots > 0 ? plan.total : (static_cast<size_t>(n) * sizeof(int) + 255) / 256 * 256;
     cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&scratch), qbytes, st);
     if (e != cudaSuccess) return cuda_fail(e, "tune scratch");
+    if (slots > 0) e = upload_region_tables(plan, scratch, st);
     cudaEvent_t a = nullptr, b = nullptr;
     if (e == cudaSuccess) e = cudaEventCreate(&a);
     if (e == cudaSuccess) e = cudaEventCreate(&b);
@@ -87,7 +88,7 @@ int time_config(Ctx &ctx, const Volume &vol, const std::vector<ViewDev> &hv, con
         if (e == cudaSuccess) e = cudaEventRecord(a, st);
         int launches = 0;
         if (slots > 0 && e == cudaSuccess)
-            e = enqueue_regions(ctx, vol, hv, spec, cfg, spec.out, scratch, st, &launches);
+            e = enqueue_regions(ctx, vol, hv, plan, spec, cfg, spec.out, scratch, st, &launches);
         for (int c = 0; c < chunks && e == cudaSuccess && slots == 0; ++c) {
             fill_args(*args, vol, hv.data(), n, c, spec, spec.out, nullptr, reinterpret_cast<int *>(scratch), cfg,
                       ctx.err_word);

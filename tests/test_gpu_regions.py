@@ -114,6 +114,31 @@ def test_region_ray_lists_hold_every_crossing_ray(ctx, warps):
     ctx.unload(vol)
 
 
+def test_region_schedule_many_launches(ctx):
+    """200 views in one region launch (in direction order, so that each
+    image's view sits elsewhere in the march than in the batch) and three
+    reductions in batch order; every image equals the whole-ray march, to
+    device and host memory."""
+    grid = gen.Grid(n=(40, 36, 33), origin=(0.5, 0.0, -1.0), dx=(1.0, 1.1, 0.9), n_epochs=4, t0=0.0, dt=3.0)
+    j, beta = _fields(41, grid.n, grid.n_epochs)
+    vol = ctx.load_snapshots(grid, j, beta)
+    rng = np.random.default_rng(41)
+    views = [gen.view_from_direction(grid, d, size=20, c=1.2, t_obs=float(rng.uniform(2.0, 8.0)))
+             for d in gen.fibonacci_directions(200)]
+    whole = _batch(ctx, vol, views, region=0)
+    got = _batch(ctx, vol, views, region=16, cta_warps=8, persistent=0)
+    for k in range(len(views)):
+        assert_parity(got[k], whole[k], rel=2e-5, what=f"view {k}")
+    host = torch.empty((len(views), 20, 20), dtype=torch.float32, pin_memory=True)
+    ctx.render_batch_host(vol, views, host, launch={"packet": (4, 8), "cta_warps": 4, "depth": 2, "persistent": 0,
+                                                    "regcap": 1, "region": 16})
+    torch.cuda.synchronize()
+    for k in range(len(views)):
+        assert_parity(host[k].numpy(), whole[k], rel=2e-5, what=f"host output view {k}")
+    assert ctx.bounds_violations() == 0
+    ctx.unload(vol)
+
+
 def test_region_schedule_host_output_and_depths(ctx):
     grid = gen.Grid(n=(33, 41, 29), origin=(0.0, 0.0, 0.0), dx=(1.0, 1.0, 1.0), n_epochs=4, t0=0.0, dt=3.0)
     j, beta = _fields(7, grid.n, grid.n_epochs)
