@@ -139,6 +139,50 @@ def test_region_schedule_many_launches(ctx):
     ctx.unload(vol)
 
 
+def test_region_schedule_without_graphs_equals_graphs(ctx, monkeypatch):
+    """With graph replay off (GBD_GRAPHS=0) a region batch is enqueued
+    directly, with stream-ordered scratch and its tables uploaded on the
+    caller's stream: the same kernels in the same order, so the images equal
+    the graph replay's bit for bit, to device and to host memory."""
+    grid = gen.Grid(n=(36, 30, 42), origin=(0.0, 0.0, 0.0), dx=(1.0, 1.0, 1.0), n_epochs=3, t0=0.0, dt=2.5)
+    j, beta = _fields(43, grid.n, grid.n_epochs)
+    vol = ctx.load_snapshots(grid, j, beta)
+    views = _views(grid, 14, 43, 24)
+    launch = {"packet": (4, 8), "cta_warps": 4, "depth": 2, "persistent": 0, "regcap": 1, "region": 16}
+    graphed = ctx.render_batch(vol, views, launch=launch)
+    torch.cuda.synchronize()
+    graphed = graphed.cpu().numpy()
+    monkeypatch.setenv("GBD_GRAPHS", "0")
+    direct = ctx.render_batch(vol, views, launch=launch)
+    host = torch.empty((len(views), 24, 24), dtype=torch.float32, pin_memory=True)
+    ctx.render_batch_host(vol, views, host, launch=launch)
+    torch.cuda.synchronize()
+    assert np.array_equal(direct.cpu().numpy(), graphed)
+    assert np.array_equal(host.numpy(), graphed)
+    assert ctx.bounds_violations() == 0
+    ctx.unload(vol)
+
+
+def test_tuner_times_region_schedules(ctx):
+    """A batch of 12 views: the autotuner also times region schedules (edges 32
+    and 64), and the render it then picks equals the untuned one to FP32
+    rounding."""
+    grid = gen.Grid(n=(40, 36, 44), n_epochs=4, t0=0.0, dt=3.0)
+    j, beta = _fields(44, grid.n, grid.n_epochs)
+    vol = ctx.load_snapshots(grid, j, beta)
+    views = _views(grid, 12, 44, 48)
+    before = _batch(ctx, vol, views, region=0)
+    res = ctx.tune(vol, views, launch=True)
+    # the default, 72 whole-ray shapes and the flat one, then 2 edges x 16 region shapes
+    assert res["candidates"] >= 1 + 72 + 1 + 32
+    after = ctx.render_batch(vol, views)
+    torch.cuda.synchronize()
+    after = after.cpu().numpy()
+    for k in range(len(views)):
+        assert_parity(after[k], before[k], rel=2e-5, what=f"tuned view {k}")
+    ctx.unload(vol)
+
+
 def test_region_schedule_host_output_and_depths(ctx):
     grid = gen.Grid(n=(33, 41, 29), origin=(0.0, 0.0, 0.0), dx=(1.0, 1.0, 1.0), n_epochs=4, t0=0.0, dt=3.0)
     j, beta = _fields(7, grid.n, grid.n_epochs)
