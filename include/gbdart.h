@@ -174,7 +174,12 @@ typedef struct {
                                     is in L2), then add each ray's region sums in
                                     order.  Images agree with the whole-ray march to
                                     FP32 rounding (a few 1e-6), not bitwise.  Not
-                                    used with sample counts; depth 1 or 2.           */
+                                    used with sample counts; depth 1 or 2.  Needs
+                                    device scratch of 4 B per pixel and partial
+                                    slot (the regions along the three axes, less
+                                    two) plus 4 B per listed ray; a batch whose
+                                    scratch does not fit fails with GBD_ERR_NOMEM,
+                                    and the autotuner leaves such schedules out.    */
     int32_t group;               /* batches: time groups.  Consecutive views that
                                     differ only in observer time (same image plane,
                                     direction and grid frame; t_obs, and with it the

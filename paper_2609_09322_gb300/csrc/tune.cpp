@@ -344,6 +344,12 @@ int gbd_tune(gbd_ctx *ctx, gbd_volume vid, const gbd_view *views, int32_t n, con
                             for (int d = 1; d <= 2; ++d) {
                                 LaunchCfg c{pk[0], pk[1], w, d, 0, cap, reg, kGroupDefault};
                                 if (region_slots(*vol, c, *spec, nreg) == 0) continue;
+                                // a region schedule whose scratch (partial slots and ray
+                                // lists) would not fit in half the free memory is left out
+                                size_t free_b = 0, total_b = 0;
+                                if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess ||
+                                    region_plan(*vol, c, *spec, hv).total > free_b / 2)
+                                    continue;
                                 float rms = 0.f;
                                 if ((rc = time_config(*ctx, *vol, hv, *spec, c, st, 3, rms))) return rc;
                                 report(c, rms, vol->brick, vol->super_brick);
