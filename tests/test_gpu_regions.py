@@ -139,6 +139,22 @@ def test_region_schedule_many_launches(ctx):
     ctx.unload(vol)
 
 
+@pytest.mark.parametrize("n_views", [1, 2])
+def test_region_schedule_one_or_two_views(ctx, n_views):
+    """The smallest batches: one and two views (one region launch, one
+    reduction) equal the whole-ray march."""
+    grid = gen.Grid(n=(33, 35, 31), n_epochs=2, t0=0.0, dt=4.0)
+    j, beta = _fields(45 + n_views, grid.n, grid.n_epochs)
+    vol = ctx.load_snapshots(grid, j, beta)
+    views = [gen.view_from_angles(grid, 40.0 + 25.0 * k, 15.0, size=36, c=1.1, t_obs=2.0) for k in range(n_views)]
+    whole = _batch(ctx, vol, views, region=0)
+    got = _batch(ctx, vol, views, region=16, persistent=0)
+    for k in range(n_views):
+        assert_parity(got[k], whole[k], rel=2e-5, what=f"view {k}")
+    assert ctx.bounds_violations() == 0
+    ctx.unload(vol)
+
+
 def test_region_schedule_without_graphs_equals_graphs(ctx, monkeypatch):
     """With graph replay off (GBD_GRAPHS=0) a region batch is enqueued
     directly, with stream-ordered scratch and its tables uploaded on the
