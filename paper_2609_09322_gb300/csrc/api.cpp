@@ -521,6 +521,29 @@ RegionProj region_proj(const ViewDev &V)
     return P;
 }
 
+// Epoch coordinate (in snapshots) at which view V sees the point x of its
+// march frame: x = g0 + p gu + q gv + s a solved for s (Cramer's rule), then
+// u = u_obs - kk s.
+static double view_epoch_at(const ViewDev &V, const double x[3])
+{
+    double m[3][3], d[3];
+    for (int i = 0; i < 3; ++i) {
+        m[i][0] = static_cast<double>(V.gu[i]) * 0x1p-40;
+        m[i][1] = static_cast<double>(V.gv[i]) * 0x1p-40;
+        m[i][2] = static_cast<double>(V.a_hi[i]) + V.a_lo[i];
+        d[i] = x[i] - static_cast<double>(V.g0[i]) * 0x1p-40;
+    }
+    auto det3 = [](const double c0[3], const double c1[3], const double c2[3]) {
+        return c0[0] * (c1[1] * c2[2] - c1[2] * c2[1]) - c1[0] * (c0[1] * c2[2] - c0[2] * c2[1]) +
+               c2[0] * (c0[1] * c1[2] - c0[2] * c1[1]);
+    };
+    const double c0[3] = {m[0][0], m[1][0], m[2][0]}, c1[3] = {m[0][1], m[1][1], m[2][1]},
+                 c2[3] = {m[0][2], m[1][2], m[2][2]};
+    const double det = det3(c0, c1, c2);
+    const double s = det != 0.0 ? det3(c0, c1, d) / det : 0.0;
+    return static_cast<double>(V.u_obs) * 0x1p-32 - (static_cast<double>(V.kk_hi) + V.kk_lo) * s;
+}
+
 // Regions per axis and partial slots of the region schedule; 0 if it does not
 // apply (no region edge set, sample counts wanted, or too many regions).
 int region_slots(const Volume &vol, const LaunchCfg &cfg, const gbd_image_spec &spec, int nreg[3])
@@ -612,7 +635,8 @@ RegionPlan region_plan(const Volume &vol, const LaunchCfg &cfg, const gbd_image_
     P.views_off = P.count_off + cbytes;
     P.proj_off = P.views_off + up(sizeof(ViewDev) * n);
     P.image_off = P.proj_off + up(sizeof(RegionProj) * n);
-    P.total = P.image_off + up(sizeof(int) * n);
+    P.order_off = P.image_off + up(sizeof(int) * n);
+    P.total = P.order_off + up(sizeof(int) * P.regions * n);
     P.tables.assign(P.total - P.views_off, 0);
     char *t = P.tables.data();
     for (size_t k = 0; k < n; ++k) {
@@ -620,6 +644,32 @@ RegionPlan region_plan(const Volume &vol, const LaunchCfg &cfg, const gbd_image_
         std::memcpy(t + (P.proj_off - P.views_off) + k * sizeof(RegionProj), &proj[k], sizeof(RegionProj));
         const int img = order[k];
         std::memcpy(t + (P.image_off - P.views_off) + k * sizeof(int), &img, sizeof(int));
+    }
+    // Per region, its views by the epoch at which they see the region's centre:
+    // the views a region's CTAs march side by side then read the same few
+    // snapshots of it.  (Beyond 2^22 view-regions the march order stands.)
+    std::vector<std::pair<double, int>> key(n);
+    int *region_order = reinterpret_cast<int *>(t + (P.order_off - P.views_off));
+    const bool sort_views = P.regions * n <= (size_t(1) << 22);
+    for (size_t r = 0; r < P.regions; ++r) {
+        if (!sort_views) {
+            for (size_t k = 0; k < n; ++k) region_order[r * n + k] = static_cast<int>(k);
+            continue;
+        }
+        const int rr[3] = {static_cast<int>(r % P.nreg[0]), static_cast<int>((r / P.nreg[0]) % P.nreg[1]),
+                           static_cast<int>(r / (static_cast<size_t>(P.nreg[0]) * P.nreg[1]))};
+        for (size_t k = 0; k < n; ++k) {
+            const ViewDev &V = hv[order[k]];
+            double x[3];
+            for (int i = 0; i < 3; ++i) {
+                const int nn = vol.grid.n[i];
+                const double c = 0.5 * (rr[i] * cfg.region + std::min((rr[i] + 1) * cfg.region, nn));
+                x[i] = (V.flags & (kFlagMirror0 << i)) ? nn - c : c;
+            }
+            key[k] = {view_epoch_at(V, x), static_cast<int>(k)};
+        }
+        std::stable_sort(key.begin(), key.end());
+        for (size_t k = 0; k < n; ++k) region_order[r * n + k] = key[k].second;
     }
     return P;
 }
@@ -661,6 +711,7 @@ cudaError_t enqueue_regions(Ctx &ctx, const Volume &vol, const std::vector<ViewD
     a.views = reinterpret_cast<const ViewDev *>(scratch + P.views_off);
     a.proj = reinterpret_cast<const RegionProj *>(scratch + P.proj_off);
     a.image = reinterpret_cast<const int *>(scratch + P.image_off);
+    a.region_order = reinterpret_cast<const int *>(scratch + P.order_off);
     a.rays = reinterpret_cast<uint32_t *>(scratch + P.rays_off);
     a.ray_count = reinterpret_cast<int *>(scratch + P.count_off);
     a.rays_per_cta = 32 * cfg.cta_warps;

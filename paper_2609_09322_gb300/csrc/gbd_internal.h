@@ -168,6 +168,7 @@ struct RegionArgs {
     const ViewDev *views;     // n_views views in march order (by direction)
     const RegionProj *proj;   // their projections
     const int *image;         // each one's image in the batch
+    const int *region_order;  // region r's views in march order: region_order[r * n_views + y]
     // Ray lists (written by screen_kernel, read by region_kernel): the pixels
     // (p | q << 16) of view v whose rays cross region r, longest chord first,
     // at rays + (r * n_views + v) * ctas_per_view * rays_per_cta, and their

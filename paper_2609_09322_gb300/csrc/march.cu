@@ -1817,19 +1817,19 @@ __global__ void __launch_bounds__(32 * kScreenWarps) screen_kernel(const __grid_
     if (lane == 0) a.ray_count[r * a.n_views + vi] = min(done, cap);
 }
 
-// The march of the region schedule: CTA (blockIdx.x) of view blockIdx.y in
-// region blockIdx.z stages the region's march tables and gives each warp the
-// next 32 rays of the view's ray list for the region, so that warp w of CTA cb
-// marches entries (cb * warps + w) * 32 .. + 31.  CTAs past the end of the
-// list return at once.
+// The march of the region schedule: CTA (blockIdx.x) of the region's
+// blockIdx.y-th view (region_order) in region blockIdx.z stages the region's
+// march tables and gives each warp the next 32 rays of the view's ray list for
+// the region, so that warp w of CTA cb marches entries (cb * warps + w) * 32 ..
+// + 31.  CTAs past the end of the list return at once.
 template <int STORE, int DEPTH, int MINB, bool PAIRED>
 __global__ void __launch_bounds__(256, MINB) region_kernel(const __grid_constant__ RegionArgs a)
 {
     extern __shared__ int32_t s_tab[];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
-    const int vi = static_cast<int>(blockIdx.y);
     const int r = static_cast<int>(blockIdx.z);
+    const int vi = __ldg(a.region_order + static_cast<long long>(r) * a.n_views + blockIdx.y);
     const int count = __ldg(a.ray_count + r * a.n_views + vi);
     const int first = static_cast<int>(blockIdx.x) * a.rays_per_cta;
     if (first >= count) return;
@@ -2077,7 +2077,7 @@ cudaError_t launch_region(const RegionArgs &a, const LaunchCfg &cfg, cudaStream_
     void *k = select_region(a.vol.store, cfg.depth, cfg.regcap, a.vol.paired);
     const long long regions = static_cast<long long>(a.nreg[0]) * a.nreg[1] * a.nreg[2];
     if (!k || a.n_views < 1 || a.n_views > 65535 || regions < 1 || regions > 65535 || a.ctas_per_view < 1 ||
-        a.rays_per_cta != 32 * cfg.cta_warps || !a.image)
+        a.rays_per_cta != 32 * cfg.cta_warps || !a.image || !a.region_order)
         return cudaErrorInvalidValue;
     const int smem = static_cast<int>(sizeof(int32_t)) * (3 * (a.region + 2) + kTabPad);
     void *params[] = {const_cast<RegionArgs *>(&a)};

@@ -122,7 +122,7 @@ struct RegionPlan {
     int slots = 0, nreg[3] = {0, 0, 0};
     size_t regions = 0;
     int ctas_per_view = 0;
-    size_t rays_off = 0, count_off = 0, views_off = 0, proj_off = 0, image_off = 0, total = 0;
+    size_t rays_off = 0, count_off = 0, views_off = 0, proj_off = 0, image_off = 0, order_off = 0, total = 0;
     std::vector<char> tables;  // host image of the scratch from views_off to total
 };
 RegionPlan region_plan(const Volume &vol, const LaunchCfg &cfg, const gbd_image_spec &spec,
