@@ -679,9 +679,9 @@ cudaError_t upload_region_tables(const RegionPlan &P, char *scratch, cudaStream_
     return cudaMemcpyAsync(scratch + P.views_off, P.tables.data(), P.tables.size(), cudaMemcpyHostToDevice, st);
 }
 
-// Enqueues a region-schedule batch on st (its tables already uploaded): clear
-// the partial slots, list each region's crossing rays of every view by chord
-// length (one screen_kernel launch), march them region by region (one
+// Enqueues a region-schedule batch on st (its tables already uploaded): list
+// each region's crossing rays of every view by chord length and clear the
+// partial slots (one screen_kernel launch), march them region by region (one
 // region_kernel launch over all views), then add up each image's slots into
 // dev_out (reduce_kernel, kImagesPerReduce images per launch).
 cudaError_t enqueue_regions(Ctx &ctx, const Volume &vol, const std::vector<ViewDev> &hv, const RegionPlan &P,
@@ -694,7 +694,7 @@ cudaError_t enqueue_regions(Ctx &ctx, const Volume &vol, const std::vector<ViewD
     float *partial = reinterpret_cast<float *>(scratch);
     *launches = 0;
     if (P.slots <= 0 || n < 1) return cudaErrorInvalidValue;
-    cudaError_t e = cudaMemsetAsync(partial, 0, sizeof(float) * static_cast<size_t>(slot_stride) * P.slots, st);
+    cudaError_t e = cudaSuccess;
     RegionArgs a;
     std::memset(&a, 0, sizeof(a));
     a.vol = vol_dev(vol);
@@ -707,6 +707,7 @@ cudaError_t enqueue_regions(Ctx &ctx, const Volume &vol, const std::vector<ViewD
     for (int i = 0; i < 3; ++i) a.nreg[i] = P.nreg[i];
     a.partial = partial;
     a.slot_stride = slot_stride;
+    a.partial_floats = slot_stride * P.slots;
     a.error_word = ctx.err_word;
     a.views = reinterpret_cast<const ViewDev *>(scratch + P.views_off);
     a.proj = reinterpret_cast<const RegionProj *>(scratch + P.proj_off);

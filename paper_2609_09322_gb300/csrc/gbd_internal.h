@@ -164,6 +164,7 @@ struct RegionArgs {
     int nreg[3];              // regions per axis
     float *partial;           // slot s of batch image b at partial + s * slot_stride + b * width * height
     long long slot_stride;    // floats per slot
+    long long partial_floats; // floats of all slots (screen_kernel clears them)
     int *error_word;
     const ViewDev *views;     // n_views views in march order (by direction)
     const RegionProj *proj;   // their projections

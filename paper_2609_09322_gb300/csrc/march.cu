@@ -1699,7 +1699,9 @@ constexpr int kScreenBatch = 2048;
 // length changes smoothly: each run of lanes with one class takes its places
 // with one shared atomic.  The list has room for every pixel the box can cover (the
 // host's bound); were it ever full, the pixels past its end would be dropped
-// and bit 1 of the error word set.
+// and bit 1 of the error word set.  The launch also clears the partial slots
+// that the region march then writes: each warp a contiguous share, before its
+// own listing, so that the stores overlap the listing's arithmetic.
 __global__ void __launch_bounds__(32 * kScreenWarps) screen_kernel(const __grid_constant__ RegionArgs a)
 {
     __shared__ int s_off_all[kScreenWarps][kChordClasses];
@@ -1707,6 +1709,15 @@ __global__ void __launch_bounds__(32 * kScreenWarps) screen_kernel(const __grid_
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int regions = a.nreg[0] * a.nreg[1] * a.nreg[2];
     const long long pair = static_cast<long long>(blockIdx.x) * kScreenWarps + warp;
+    {
+        const long long warps = static_cast<long long>(gridDim.x) * kScreenWarps;
+        const long long n4 = a.partial_floats >> 2;  // the slots start 256-byte aligned
+        const long long share = (n4 + warps - 1) / warps;
+        const long long lo = min(pair * share, n4), hi = min(lo + share, n4);
+        float4 *p4 = reinterpret_cast<float4 *>(a.partial);
+        for (long long i = lo + lane; i < hi; i += 32) __stcs(p4 + i, make_float4(0.f, 0.f, 0.f, 0.f));
+        if (pair == 0 && lane < (a.partial_floats & 3)) a.partial[(n4 << 2) + lane] = 0.f;
+    }
     if (pair >= static_cast<long long>(a.n_views) * regions) return;
     const int vi = static_cast<int>(pair % a.n_views), r = static_cast<int>(pair / a.n_views);
     int *s_off = s_off_all[warp];
@@ -2064,7 +2075,8 @@ cudaError_t launch_screen(const RegionArgs &a, cudaStream_t stream)
 {
     const long long regions = static_cast<long long>(a.nreg[0]) * a.nreg[1] * a.nreg[2];
     if (a.n_views < 1 || a.n_views > 65535 || !a.rays || !a.ray_count || !a.views || !a.proj || a.rays_per_cta < 32 ||
-        a.ctas_per_view < 1 || regions < 1 || regions > 65535)
+        a.ctas_per_view < 1 || regions < 1 || regions > 65535 || a.partial_floats < 0 ||
+        (a.partial_floats > 0 && !a.partial))
         return cudaErrorInvalidValue;
     const long long ctas = (a.n_views * regions + kScreenWarps - 1) / kScreenWarps;
     void *params[] = {const_cast<RegionArgs *>(&a)};
