@@ -174,7 +174,9 @@ typedef struct {
                                     is in L2), then add each ray's region sums in
                                     order.  Images agree with the whole-ray march to
                                     FP32 rounding (a few 1e-6), not bitwise.  Not
-                                    used with sample counts; depth 1 or 2.  Needs
+                                    used with sample counts or for batches of more
+                                    than 65535 views (their rays march whole);
+                                    depth 1 or 2.  Needs
                                     device scratch of 4 B per pixel and partial
                                     slot (the regions along the three axes, less
                                     two) plus 4 B per listed ray; a batch whose

@@ -544,11 +544,13 @@ static double view_epoch_at(const ViewDev &V, const double x[3])
     return static_cast<double>(V.u_obs) * 0x1p-32 - (static_cast<double>(V.kk_hi) + V.kk_lo) * s;
 }
 
-// Regions per axis and partial slots of the region schedule; 0 if it does not
-// apply (no region edge set, sample counts wanted, or too many regions).
-int region_slots(const Volume &vol, const LaunchCfg &cfg, const gbd_image_spec &spec, int nreg[3])
+// Regions per axis and partial slots of the region schedule for a batch of
+// n_views views; 0 if it does not apply (no region edge set, sample counts
+// wanted, more than 65535 regions or views: a batch of more views marches its
+// rays whole).
+int region_slots(const Volume &vol, const LaunchCfg &cfg, const gbd_image_spec &spec, int nreg[3], long long n_views)
 {
-    if (cfg.region <= 0 || spec.samples) return 0;
+    if (cfg.region <= 0 || spec.samples || n_views < 1 || n_views > 65535) return 0;
     long long regions = 1;
     int slots = 0;
     for (int i = 0; i < 3; ++i) {
@@ -614,7 +616,7 @@ RegionPlan region_plan(const Volume &vol, const LaunchCfg &cfg, const gbd_image_
                        const std::vector<ViewDev> &hv)
 {
     RegionPlan P;
-    P.slots = region_slots(vol, cfg, spec, P.nreg);
+    P.slots = region_slots(vol, cfg, spec, P.nreg, static_cast<long long>(hv.size()));
     if (P.slots <= 0) return P;
     const size_t n = hv.size();
     auto up = [](size_t b) { return (b + 255) / 256 * 256; };
@@ -750,7 +752,7 @@ int render_direct(Ctx &ctx, const Volume &vol, const std::vector<ViewDev> &hv, c
     const size_t pix = static_cast<size_t>(spec.width) * spec.height * n;
     char *scratch = nullptr;
     int nreg[3];
-    const int slots = region_slots(vol, cfg, spec, nreg);
+    const int slots = region_slots(vol, cfg, spec, nreg, n);
     if (slots > 0) {
         const RegionPlan plan = region_plan(vol, cfg, spec, hv);
         const size_t pbytes = plan.total;
@@ -941,7 +943,7 @@ static int build_graph(Ctx &ctx, const Volume &vol, const GraphKey &key, const g
                        const std::vector<ViewDev> &hv, GraphEntry &g)
 {
     int nreg[3];
-    const int slots = region_slots(vol, key.cfg, spec, nreg);
+    const int slots = region_slots(vol, key.cfg, spec, nreg, key.n);
     if (slots > 0) return build_region_graph(ctx, vol, key, spec, hv, slots, g);
     const int n = key.n;
     const size_t img_off = queue_bytes(n);

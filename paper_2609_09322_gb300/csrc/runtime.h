@@ -117,7 +117,7 @@ int check_launch(const LaunchCfg &c);
 int march_chunks(int n);
 double view_work(const Volume &vol, const ViewDev &V, int width, int height);
 // Region schedule (see RegionArgs): slots per ray, 0 when it does not apply.
-int region_slots(const Volume &vol, const LaunchCfg &cfg, const gbd_image_spec &spec, int nreg[3]);
+int region_slots(const Volume &vol, const LaunchCfg &cfg, const gbd_image_spec &spec, int nreg[3], long long n_views);
 struct RegionPlan {
     int slots = 0, nreg[3] = {0, 0, 0};
     size_t regions = 0;

@@ -70,7 +70,7 @@ int time_config(Ctx &ctx, const Volume &vol, const std::vector<ViewDev> &hv, con
     const int n = static_cast<int>(hv.size());
     char *scratch = nullptr;
     int nreg[3];
-    const int slots = region_slots(vol, cfg, spec, nreg);
+    const int slots = region_slots(vol, cfg, spec, nreg, n);
     const RegionPlan plan = slots > 0 ? region_plan(vol, cfg, spec, hv) : RegionPlan();
     const size_t qbytes = slots > 0 ? plan.total : (static_cast<size_t>(n) * sizeof(int) + 255) / 256 * 256;
     cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&scratch), qbytes, st);
@@ -343,7 +343,7 @@ int gbd_tune(gbd_ctx *ctx, gbd_volume vid, const gbd_view *views, int32_t n, con
                         for (int w : rwarps)
                             for (int d = 1; d <= 2; ++d) {
                                 LaunchCfg c{pk[0], pk[1], w, d, 0, cap, reg, kGroupDefault};
-                                if (region_slots(*vol, c, *spec, nreg) == 0) continue;
+                                if (region_slots(*vol, c, *spec, nreg, n) == 0) continue;
                                 // a region schedule whose scratch (partial slots and ray
                                 // lists) would not fit in half the free memory is left out
                                 size_t free_b = 0, total_b = 0;
